@@ -1,0 +1,239 @@
+/*
+ * mhc.h -- C ABI of the GB300 multi-hadron correlator library.
+ *
+ * The library evaluates, on one GPU in complex FP64, the nuclear correlator of
+ * Vachaspati & Detmold, "Fast Evaluation of Multi-Hadron Correlation Functions"
+ * (Lattice 2014):
+ *
+ *     C = sum_{i in src} sum_{j in snk} w_i w_j prod_f det G_f^{(ij)},
+ *     G_f^{(ij)}[m][n] = S_f[a_i^{f,m}][a_j^{f,n}]
+ *
+ * (Sec. 1: the correlator as a double sum over wavefunction terms of w_i w_j det G^{(ij)};
+ * the definition of G^{(ij)} from the propagator; det G as the product of per-flavour
+ * blocks because G is block diagonal in flavour).  The 1/Z and the gauge average of
+ * Sec. 1 are not part of a call: one call is one gauge configuration and one time.
+ *
+ * The determinants follow the determinant-update scheme of Sec. 2 and Sec. 3: source
+ * terms are grouped (greedy dominating set of the source-term graph, Sec. 3) into
+ * families that share all but one row (or two rows) per flavour; per (family, sink,
+ * flavour) the shared rows are LU-factorised once with partial pivoting, and one
+ * triangular solve gives det(G) G^{-1} e_r, so each member costs one O(n) dot product
+ * (matrix determinant lemma and the cached-solve remark of Sec. 2.1).  A member whose
+ * lemma factor, or whose family's pivots, fall below a threshold is refactored from
+ * scratch.  Sums are reduced in a fixed order: results are bitwise reproducible.
+ *
+ * Conventions for every entry point:
+ *   - All pointers marked "device" are CUDA device pointers on the current device;
+ *     "host" pointers are read during the call only, and the library keeps copies.
+ *   - Device calls are asynchronous on the given stream and never synchronise, except
+ *     where stated.  Outputs are written (not accumulated) unless stated.
+ *   - Every entry point returns an mhc_status; on failure a message is available from
+ *     mhc_last_error() (thread-local) and device outputs are left undefined.
+ *   - Complex numbers are two doubles (re, im), interleaved.
+ *   - S_f is complex128, L_f x L_f, row-major: entry (a, b) at doubles 2(a L_f + b).
+ *   - Term labels are int32 [N][sum_f n_f], flavour-major inside a term: the labels of
+ *     flavour f of term i start at i * sum_f n_f + sum_{f' < f} n_f'.
+ */
+#ifndef MHC_H
+#define MHC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhc_plan_s* mhc_plan_t;   /* opaque, owned by the library */
+typedef struct mhc_batch_s* mhc_batch_t; /* opaque, owned by the library */
+typedef void* mhc_stream_t;              /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  MHC_OK = 0,
+  MHC_EINVAL = 1,       /* bad argument (validated on the host)                  */
+  MHC_ENOMEM = 2,       /* host or device allocation failed                      */
+  MHC_ECUDA = 3,        /* a CUDA runtime call failed                            */
+  MHC_ETIMEOUT = 4,     /* a bounded device wait ran out                         */
+  MHC_ENONFINITE = 5,   /* a non-finite value reached a result (NaN/Inf input)   */
+  MHC_EUNSUPPORTED = 6  /* valid request that this build does not implement      */
+} mhc_status;
+
+#define MHC_NMAX 32     /* largest n_f (quarks of one flavour in a term) */
+#define MHC_FMAX 8      /* largest number of flavours */
+
+/* Planner options.  mhc_plan_opts_default() fills the defaults listed here. */
+typedef struct {
+  double tau_parent;   /* refactor all members of a (family, sink, flavour) when the
+                          smallest pivot of the shared-row LU is below tau_parent times
+                          the largest (magnitudes compared as powers of two). 1e-4   */
+  double tau_child;    /* refactor one member when |det| < tau_child * |row| * |y|,
+                          the normalised lemma factor (powers of two).          1e-3  */
+  int32_t sink_tile;   /* sinks per thread block; 0 = chosen by n class.        0     */
+  int32_t rank2;       /* 1: families may differ in two rows per flavour (rank-2
+                          update by a 2x2 generalised cofactor); 0: one row.    1     */
+  int32_t max_family;  /* largest number of members per family, 1..64.          32    */
+  int32_t reserved[8];
+} mhc_plan_opts;
+
+/* Planner and run statistics. */
+typedef struct {
+  int64_t n_src, n_snk;          /* term counts                                       */
+  int32_t n_flavours;
+  int32_t max_n;                 /* largest n_f                                       */
+  int64_t dominators;            /* greedy dominating-set size (Sec. 3)               */
+  int64_t families;              /* work families after splitting by changed rows     */
+  int64_t rank2_family_flavours; /* (family, flavour) blocks updated at rank 2        */
+  int64_t members;               /* == n_src                                          */
+  int64_t graph_edges;           /* edges of the source-term graph                    */
+  double flops_per_call;         /* algorithmic FP64 flops of one mhc_correlator call,
+                                    without refactors (counting rule in the design doc)     */
+  double fresh_lu_flops_per_pair;/* flops of one refactored pair (all flavours)        */
+  double bytes_per_call;         /* algorithmic bytes: S_f once, labels, weights, out */
+  double plan_seconds;           /* host time spent in mhc_plan                       */
+  /* device counters of the last mhc_correlator / backward call (mhc_get_status): */
+  int64_t refactor_parent;       /* (member, sink, flavour) refactored by the pivot guard */
+  int64_t refactor_child;        /* (member, sink, flavour) refactored by the lemma guard */
+  int64_t reserved[6];
+} mhc_stats;
+
+/* Thread-local message describing the last failure of this thread's last call. */
+const char* mhc_last_error(void);
+
+/* Fill *opts with the defaults. */
+void mhc_plan_opts_default(mhc_plan_opts* opts);
+
+/*
+ * Build a plan (host only; Sec. 3 execution order).  Validates the inputs, builds the
+ * source-term graph (two terms are adjacent when, in every flavour, their label
+ * multisets differ in at most one label, or two with opts->rank2), takes the greedy
+ * maximum-degree dominating set (ties to the lowest term index), aligns every member
+ * to its dominator's label positions (the permutation sign goes into the member's
+ * sign) and splits each dominated set into work families whose members change the
+ * same row (or row pair) per flavour.
+ *   n_flavours      : F, 0 < F <= MHC_FMAX
+ *   n_f, L_f        : host int32[F]; 0 <= n_f <= MHC_NMAX, 1 <= L_f <= 4096
+ *   n_src, n_snk    : term counts, > 0
+ *   labels_src/_snk : host int32 [N][sum n_f], each label of flavour f in [0, L_f)
+ *   w_src, w_snk    : host float64 [N]; default weights of the correlator calls
+ *   opts            : NULL for the defaults
+ * The plan is reusable across propagators S_f (Sec. 3: the graph and the dominating
+ * set do not depend on the gauge configuration).  Its device tables are uploaded by
+ * the first device call that uses it (a synchronous copy on the current device);
+ * issue that first call outside any stream capture.  Repeated labels are allowed and
+ * give det = 0.  n_f = 0 makes flavour f a factor 1.
+ * Errors: MHC_EINVAL (bad sizes or labels, null pointers), MHC_ENOMEM.
+ */
+mhc_status mhc_plan(mhc_plan_t* out, int32_t n_flavours, const int32_t* n_f, const int32_t* L_f,
+                    int64_t n_src, const int32_t* labels_src, const double* w_src, int64_t n_snk,
+                    const int32_t* labels_snk, const double* w_snk, const mhc_plan_opts* opts);
+
+/* Release a plan and its device tables (synchronises the device first). NULL is a no-op. */
+void mhc_plan_destroy(mhc_plan_t plan);
+
+/* Copy the plan's statistics (including the last run's device counters, as of the
+ * last mhc_get_status). */
+mhc_status mhc_plan_stats(mhc_plan_t plan, mhc_stats* out);
+
+/*
+ * Export the work families (host; for inspection and tests).  Pass NULL for the
+ * arrays to query the sizes only.  With W = *n_families and Tn = sum_f n_f:
+ *   fam_member_offset : int64 [W+1]; members of family w are [off[w], off[w+1])
+ *   fam_rank          : int32 [W][F]; 0 (n_f = 0), 1 or 2 changed rows
+ *   fam_rows          : int32 [W][F][2]; changed-row positions in the reference tuple
+ *                       (ascending; -1 when unused)
+ *   fam_ref           : int32 [W][Tn]; the dominator's labels (reference tuple)
+ *   member_term       : int64 [n_src]; source term of each member
+ *   member_sign       : int32 [n_src]; +-1: det of the term's own label order equals
+ *                       member_sign times prod_f det [shared rows; member rows]
+ *   member_labels     : int32 [n_src][F][2]; the member's labels at the changed rows
+ * "[shared rows; member rows]" is the matrix whose rows are, in order, the reference
+ * tuple's labels at the positions not in fam_rows (ascending), then the member's labels
+ * at fam_rows (ascending), and whose columns are the sink term's labels.
+ */
+mhc_status mhc_plan_families(mhc_plan_t plan, int64_t* n_families, int64_t* fam_member_offset,
+                             int32_t* fam_rank, int32_t* fam_rows, int32_t* fam_ref,
+                             int64_t* member_term, int32_t* member_sign, int32_t* member_labels);
+
+/*
+ * Forward correlator on the GPU.
+ *   S_f        : host array of F device pointers, each complex128 L_f x L_f (may alias)
+ *   w_src_dev  : device float64 [n_src] source weights, or NULL for the plan's
+ *   w_snk_dev  : device float64 [n_snk] sink weights, or NULL for the plan's
+ *   out_dev    : device float64 [2]: (Re C, Im C), written
+ *   stream     : cudaStream_t
+ * The plan holds the workspace: calls with the same plan must not overlap on the GPU.
+ * Non-finite results set a device status bit reported by mhc_get_status.
+ */
+mhc_status mhc_correlator(mhc_plan_t plan, const double* const* S_f, const double* w_src_dev,
+                          const double* w_snk_dev, double* out_dev, mhc_stream_t stream);
+
+/*
+ * Adjoint (hand-written; Jacobi's formula d det G / dG = cofactor matrix, with the LU
+ * factors recomputed).  With g = g_out[0] + i g_out[1] = dL/dRe C + i dL/dIm C and the
+ * holomorphic derivatives D_S = dC/dS_f, D_w = dC/dw:
+ *   dS_f[a][b] = g * conj(D_S[a][b])      (complex128 L_f x L_f, device, written)
+ *   dw_src[i]  = Re(conj(g) * D_w_src[i]) (float64, device, written)
+ *   dw_snk[j]  = Re(conj(g) * D_w_snk[j]) (float64, device, written)
+ * which is PyTorch's convention for the gradient of a real loss.  g_out_dev is a device
+ * pointer to 2 doubles.  Any of dS_f (the whole array or single entries), dw_src_dev or
+ * dw_snk_dev may be NULL to skip that output.  The dS_f buffers must not alias each
+ * other.
+ */
+mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
+                                   const double* w_src_dev, const double* w_snk_dev,
+                                   const double* g_out_dev, double* const* dS_f,
+                                   double* dw_src_dev, double* dw_snk_dev, mhc_stream_t stream);
+
+/*
+ * Per-pair determinants through the same update path (families, lemma, guards):
+ *   i_dev, j_dev : device int64 [n_pairs] source and sink term indices
+ *   dets_dev     : device float64 [n_pairs][F][2], det of each flavour block in the
+ *                  terms' own label order, written
+ *   path_dev     : device int32 [n_pairs] or NULL; bit f set when flavour f of the
+ *                  pair was refactored from scratch by a guard
+ * Indices out of range give MHC_EINVAL through the device status (mhc_get_status).
+ */
+mhc_status mhc_pair_dets(mhc_plan_t plan, const double* const* S_f, int64_t n_pairs,
+                         const int64_t* i_dev, const int64_t* j_dev, double* dets_dev,
+                         int32_t* path_dev, mhc_stream_t stream);
+
+/*
+ * Wait for the stream, read the plan's device status word and counters, clear them.
+ * Returns MHC_OK, MHC_ENONFINITE, MHC_EINVAL (bad pair index) or MHC_ETIMEOUT.
+ */
+mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream);
+
+/*
+ * Batching: many independent correlators (each its own plan, flavour sizes and term
+ * counts) in one persistent launch, captured once into a CUDA graph.
+ * mhc_batch_create autotunes the launch shape on the current device (it runs the
+ * kernels on scratch inputs and synchronises) and uploads the plans.
+ *   plans : host array of `count` plans; they must outlive the batch
+ */
+mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* plans);
+void mhc_batch_destroy(mhc_batch_t batch);
+
+/*
+ * Evaluate every correlator of the batch:
+ *   S    : host array [count] of host arrays [F_b] of device pointers (each plan's S_f)
+ *   outs : host array [count] of device pointers to 2 doubles, written
+ * The plans' own weights are used.  The first call with a given set of pointers captures
+ * a CUDA graph; later calls with the same pointers replay it.
+ */
+mhc_status mhc_batch_correlator(mhc_batch_t batch, const double* const* const* S,
+                                double* const* outs, mhc_stream_t stream);
+
+/* Autotuned launch shape of batch item b: threads per block and sink tile. */
+mhc_status mhc_batch_info(mhc_batch_t batch, int32_t* threads_per_block, int32_t* tiles_total);
+
+/*
+ * FP64 peak probe: runs independent DFMA chains on every SM for about `iters` x 8 FMAs
+ * per thread and returns the measured rate in FLOP/s (2 per DFMA) in *flops.  Used to
+ * state the roofline denominator on the same GPU and clocks as a measurement.
+ */
+mhc_status mhc_fp64_peak(int32_t iters, double* flops, mhc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHC_H */
