@@ -1,0 +1,306 @@
+"""Benchmark: the He-4-like correlator (2 flavours, n_f = 6, L = 48, 4096 x 4096 source x sink
+terms in families of 16) evaluated on the GPU through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mhc|reference]
+
+One step = one mhc_correlator call (every step of the hot path: shared-row factorisation,
+cached solves, member dot products, refactors, fixed-order reduction) for one propagator
+set.  The plan (Sec. 3: graph + dominating set) is built once before timing, as the paper
+amortises it over gauge configurations.  Between timed steps L2 is flushed by writing a
+256 MiB buffer (outside the timed events).  Under torchrun every rank evaluates its own
+independent correlator (its own propagators: another gauge configuration), so the work per
+GPU is fixed ("weak" scaling) and no collective is on the data path; rank 0 prints one
+JSON line with the whole-job pairs/s over the slowest rank.
+
+--impl reference times the oracle (plain CPU FP64, fresh LU per pair) on the host cores on
+a bounded sample of the same workload, with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "src×snk det pairs/sec (cplx FP64), % roofline; batched & adjoint vs plain GPU"
+UNIT = "pairs/s"
+# FP64 peak from unit counts and clocks: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
+NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum per forward launch, from one ncu capture of
+# this workload (profiles/fwd_kernel_he4.md); None until captured for the current kernel.
+FWD_TRAFFIC_BYTES = 38.18e6  # 0.597 MB read + 37.58 MB write (fwd_kernel<8>, 3.055 ms launch)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mhc", choices=["mhc", "reference"])
+    ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int):
+    from paper_1411_3691_gb300 import workloads as wl
+    return wl.helium4(seed=1000 + 17 * rank)
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(w, seconds: float):
+    """Oracle pairs/s on the host cores over a bounded sample of source terms (all sinks)."""
+    import oracle
+    threads = cores()
+    n_snk = len(w.w_snk)
+    # calibrate on a small block, then size the sample for about `seconds`
+    t0 = time.perf_counter()
+    oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=threads,
+                      src_range=(0, min(len(w.w_src), 4 * threads)))
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate0 = min(len(w.w_src), 4 * threads) * n_snk / dt
+    n_src = int(min(len(w.w_src), max(threads, rate0 * seconds / n_snk)))
+    t0 = time.perf_counter()
+    C, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk,
+                                 threads=threads, src_range=(0, n_src))
+    dt = time.perf_counter() - t0
+    return {"value": n_src * n_snk / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n_src} of {len(w.w_src)} source terms x all {n_snk} sinks "
+                      f"({n_src * n_snk} pairs, fresh partial-pivot LU per pair per flavour), "
+                      f"{dt:.2f} s on {threads} threads"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(0)
+    steps = []
+    per = max(args.cpu_sample_seconds / max(args.steps + args.warmup, 1), 0.5)
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(w, per)
+        if s >= args.warmup:
+            steps.append(r)
+    value = sum(r["value"] for r in steps) / len(steps)
+    cb = dict(steps[-1])
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "flavours": 2, "n_f": 6, "L": 48, "n_src": len(w.w_src),
+                       "n_snk": len(w.w_snk)},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1411_3691_gb300 import build as B
+    B.build()
+    from paper_1411_3691_gb300 import mhc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    w = workload(rank)
+    plan = mhc.Plan.from_workload(w)
+    st = plan.stats()
+    S = [torch.from_numpy(s).cuda() for s in w.S]
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # warm-up (first call uploads the plan)
+    for _ in range(max(args.warmup, 3)):
+        plan.correlator(S, out=out)
+    torch.cuda.synchronize()
+    plan.status()
+
+    # FP64 peak on this GPU, now (same clocks regime)
+    peak_flops = mhc.mhc_fp64_peak(250000)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            plan.correlator(S, out=out)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.summary()
+    step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+    plan.status()
+    st = plan.stats()
+    if pg:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pairs = len(w.w_src) * len(w.w_snk)
+    ms_per_step = total_ms / args.steps
+    value = world * pairs / (ms_per_step * 1e-3)
+
+    # roofline of the forward kernel (FP64 ALU bound): algorithmic flops per launch over the
+    # step's device time, against the FP64 peak measured above
+    refactor_pairs = (st["refactor_parent"] + st["refactor_child"]) / max(args.steps, 1)
+    flops = st["flops_per_call"] + refactor_pairs * st["fresh_lu_flops_per_pair"] / 2
+    achieved = flops / (ms_per_step * 1e-3) / 1e12
+    peak = peak_flops / 1e12
+
+    # end to end through the public API: pinned host propagators -> device, correlator,
+    # result -> host, every step
+    hS = [torch.from_numpy(s).pin_memory() for s in w.S]
+    hout = torch.empty(2, dtype=torch.float64).pin_memory()
+    dS = [torch.empty_like(s, device="cuda") for s in hS]
+    for _ in range(2):
+        for d, h in zip(dS, hS):
+            d.copy_(h, non_blocking=True)
+        plan.correlator(dS, out=out)
+        hout.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        for d, h in zip(dS, hS):
+            d.copy_(h, non_blocking=True)
+        plan.correlator(dS, out=out)
+        hout.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if pg:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(h.numel() * h.element_size() for h in hS)
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "flavours": 2, "n_f": 6, "L": 48, "n_src": len(w.w_src),
+                       "n_snk": len(w.w_snk), "pairs_per_gpu": pairs, "families": st["families"],
+                       "parallelism": f"{world} independent correlators (one per GPU)",
+                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": FWD_TRAFFIC_BYTES,
+                         "peak_source": "FP64 DFMA chains on all SMs, measured in this run "
+                                        f"(nominal {NOMINAL_FP64_TFLOPS:.3f} from unit counts and clocks)",
+                         "flops_per_step": flops},
+            "e2e": {"value": world * pairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 16},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "refactors_per_step": refactor_pairs,
+            "C": [float(out[0].item()), float(out[1].item())],
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_rate(w, args.cpu_sample_seconds)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,278 @@
+// device.cuh -- complex FP64 device arithmetic and the per-thread factorisations of the
+// determinant-update scheme.
+//
+// GB300 executes FP64 at 2 DFMA per clock per SM (a warp-wide DFMA occupies a
+// sub-partition's FP64 pipe for 64 cycles, predicated-off lanes included), while integer,
+// select, shuffle and load instructions are ~60x cheaper.  Every routine here therefore
+// (1) gives each thread its own matrix, so all 32 lanes do useful FP64 work, (2) keeps the
+// FP64 instruction count minimal (a complex multiply-add is 4 DFMA, pivot comparisons and
+// guard tests run on the IEEE bit patterns in the integer pipe), and (3) is fully unrolled
+// for a compile-time n, so the factors live in registers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mhc {
+namespace dev {
+
+typedef double2 cd;
+
+__device__ __forceinline__ cd cmul(cd a, cd b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + a b
+__device__ __forceinline__ cd cfma(cd a, cd b, cd acc) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc - a b
+__device__ __forceinline__ cd cfms(cd a, cd b, cd acc) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ cd cneg(cd a) { return make_double2(-a.x, -a.y); }
+
+// pivot measure |re| + |im| (one DADD; the absolute values are free operand modifiers)
+__device__ __forceinline__ double abs1(cd a) { return fabs(a.x) + fabs(a.y); }
+
+// a > b for non-negative, non-NaN doubles, compared as integers (no FP64 instruction)
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+
+// unbiased binary exponent of |x| from the bit pattern (zero and subnormals give -1023)
+__device__ __forceinline__ int expo(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+__device__ __forceinline__ int expo(cd z) { return max(expo(z.x), expo(z.y)); }
+
+// 1/d by Newton-Raphson iteration (x <- x + x(1 - d x), quadratic convergence), seeded
+// with the PTX approximate reciprocal; two steps reach full double precision.
+__device__ __forceinline__ double rcp_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+// 1/z = conj(z) / |z|^2
+__device__ __forceinline__ cd crcp(cd z) {
+  const double d = fma(z.x, z.x, z.y * z.y);
+  const double r = rcp_nr(d);
+  return make_double2(z.x * r, -z.y * r);
+}
+
+__device__ __forceinline__ cd ldS(const cd* __restrict__ p) { return __ldg(p); }
+
+// ------------------------------------------------------------------------------------
+// Shared-row factorisation of one (family, sink, flavour) block.
+//
+// A = S[arow[i]][col[q]], i < M = n - RHO shared rows, q < n sink columns.  The family's
+// changed rows are ordered last, so the LU of the parent (Sec. 2) with partial pivoting
+// among the shared rows leaves U = [U1 | U2] (U1 M x M upper triangular), the forward
+// solve of the permuted unit vector e_r is trivial, and one back substitution per
+// changed row gives the null vectors  z_t = [-U1^{-1} U2 e_t ; e_t]  of A.  Then for any
+// member B (RHO rows),
+//     det [A ; B] = sd * det(B Z),   sd = sign(P) det(U1),
+// which for RHO = 1 is the cofactor form of the matrix determinant lemma (Sec. 2.1):
+// y = sd z = det(G) G^{-1} e_r and det(G + e_r v^T) = g' . y.
+//
+// Output (slot stride ys):
+//   RHO = 1: y[0..n) = sd z                                 (n slots)
+//   RHO = 2: z1[0..n), z2[0..n), sd                          (2n + 1 slots)
+// Returns true when the pivot guard fires: an exactly zero pivot, or
+// max/min pivot magnitude above 2^kp (magnitudes compared by binary exponent).
+// *ey receives the exponent scale used by the member guard (see member_det).
+// ------------------------------------------------------------------------------------
+template <int NC, int NFIX, int RHO>
+__device__ __forceinline__ bool shared_rows(const cd* __restrict__ S, int L, int n_rt,
+                                            const int32_t* __restrict__ arow,
+                                            const int32_t* __restrict__ colp, cd* __restrict__ Y,
+                                            int ys, int* ey, int kp) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - RHO;
+  constexpr int MC = (NC - RHO) > 0 ? (NC - RHO) : 1;
+  int col[NC];
+#pragma unroll UNR
+  for (int q = 0; q < n; q++) col[q] = colp[q];
+  cd A[MC][NC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+    const cd* row = S + (size_t)arow[i] * L;
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) A[i][q] = ldS(row + col[q]);
+  }
+  int parity = 0, emin = 4096, emax = -4096;
+  bool zero = false;
+  cd rc[MC];
+  cd det = make_double2(1.0, 0.0);
+#pragma unroll UNR
+  for (int k = 0; k < M; k++) {
+    // partial pivoting: bring the first row of largest |re|+|im| to position k
+    double best = abs1(A[k][k]);
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const double m = abs1(A[i][k]);
+      const bool sw = gt_nonneg(m, best);
+      best = sw ? m : best;
+      parity ^= (int)sw;
+#pragma unroll UNR
+      for (int q = k; q < n; q++) {
+        const cd t = A[k][q];
+        A[k][q] = sw ? A[i][q] : t;
+        A[i][q] = sw ? t : A[i][q];
+      }
+    }
+    const int e = expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    const cd piv = A[k][k];
+    det = (k == 0) ? piv : cmul(det, piv);
+    rc[k] = crcp(piv);
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const cd l = cmul(A[i][k], rc[k]);
+#pragma unroll UNR
+      for (int q = k + 1; q < n; q++) A[i][q] = cfms(l, A[k][q], A[i][q]);
+    }
+  }
+  const cd sd = parity ? cneg(det) : det;
+  int ez = -4096;
+#pragma unroll
+  for (int t = 0; t < RHO; t++) {
+    cd z[NC];
+#pragma unroll UNR
+    for (int k = M - 1; k >= 0; k--) {
+      cd s = A[k][M + t];
+#pragma unroll UNR
+      for (int q = k + 1; q < M; q++) s = cfma(A[k][q], z[q], s);
+      z[k] = cmul(s, cneg(rc[k]));
+    }
+    if (RHO == 1) {
+#pragma unroll UNR
+      for (int q = 0; q < M; q++) {
+        const cd y = cmul(sd, z[q]);
+        Y[q * ys] = y;
+        ez = max(ez, expo(y));
+      }
+      Y[M * ys] = sd;
+      ez = max(ez, expo(sd));
+    } else {
+#pragma unroll UNR
+      for (int q = 0; q < M; q++) {
+        Y[(t * n + q) * ys] = z[q];
+        ez = max(ez, expo(z[q]));
+      }
+      Y[(t * n + M + t) * ys] = make_double2(1.0, 0.0);      // z_t = [.. ; e_t]
+      Y[(t * n + M + 1 - t) * ys] = make_double2(0.0, 0.0);
+    }
+  }
+  if (RHO == 2) {
+    Y[(2 * n) * ys] = sd;
+    ez = max(ez, 0);  // the unit entries of z
+    *ey = expo(sd) + 2 * ez;
+  } else {
+    *ey = ez;
+  }
+  return M > 0 && (zero || emax - emin > kp);
+}
+
+// det of member rows B against the cached solve: RHO = 1: b . y; RHO = 2: sd det(B Z).
+// *fail is set when |det| < 2^-kc |b| |y| (the normalised lemma factor, by exponents).
+template <int NC, int NFIX, int RHO>
+__device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_rt,
+                                         const int32_t* __restrict__ lab,
+                                         const int32_t* __restrict__ colp,
+                                         const cd* __restrict__ Y, int ys, int ey, int kc,
+                                         bool* fail) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  if (RHO == 1) {
+    const cd* row = S + (size_t)lab[0] * L;
+    cd b = ldS(row + colp[0]);
+    int eb = expo(b);
+    cd d = cmul(b, Y[0]);
+#pragma unroll UNR
+    for (int q = 1; q < n; q++) {
+      b = ldS(row + colp[q]);
+      eb = max(eb, expo(b));
+      d = cfma(b, Y[q * ys], d);
+    }
+    *fail = expo(d) < eb + ey - kc;
+    return d;
+  } else {
+    const cd* r1 = S + (size_t)lab[0] * L;
+    const cd* r2 = S + (size_t)lab[1] * L;
+    cd d11 = make_double2(0.0, 0.0), d12 = d11, d21 = d11, d22 = d11;
+    int e1 = -4096, e2 = -4096;
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) {
+      const int c = colp[q];
+      const cd b1 = ldS(r1 + c), b2 = ldS(r2 + c);
+      const cd z1 = Y[q * ys], z2 = Y[(n + q) * ys];
+      e1 = max(e1, expo(b1));
+      e2 = max(e2, expo(b2));
+      d11 = cfma(b1, z1, d11);
+      d12 = cfma(b1, z2, d12);
+      d21 = cfma(b2, z1, d21);
+      d22 = cfma(b2, z2, d22);
+    }
+    const cd dd = cfms(d12, d21, cmul(d11, d22));
+    const cd d = cmul(Y[2 * n * ys], dd);
+    *fail = expo(d) < e1 + e2 + ey - kc;
+    return d;
+  }
+}
+
+// Fresh determinant of one n x n block by LU with partial pivoting (the refactor path):
+// rows S[rows[m]], columns col[q].
+template <int NC, int NFIX>
+__device__ __forceinline__ cd fresh_det(const cd* __restrict__ S, int L, int n_rt,
+                                        const int32_t* rows, const int32_t* __restrict__ colp) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  cd A[NC][NC];
+#pragma unroll UNR
+  for (int i = 0; i < n; i++) {
+    const cd* row = S + (size_t)rows[i] * L;
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) A[i][q] = ldS(row + colp[q]);
+  }
+  int parity = 0;
+  bool zero = false;
+  cd det = make_double2(1.0, 0.0);
+#pragma unroll UNR
+  for (int k = 0; k < n; k++) {
+    double best = abs1(A[k][k]);
+#pragma unroll UNR
+    for (int i = k + 1; i < n; i++) {
+      const double m = abs1(A[i][k]);
+      const bool sw = gt_nonneg(m, best);
+      best = sw ? m : best;
+      parity ^= (int)sw;
+#pragma unroll UNR
+      for (int q = k; q < n; q++) {
+        const cd t = A[k][q];
+        A[k][q] = sw ? A[i][q] : t;
+        A[i][q] = sw ? t : A[i][q];
+      }
+    }
+    zero |= (__double_as_longlong(best) == 0);
+    const cd piv = A[k][k];
+    det = (k == 0) ? piv : cmul(det, piv);
+    if (k + 1 < n) {
+      const cd rc = crcp(piv);
+#pragma unroll UNR
+      for (int i = k + 1; i < n; i++) {
+        const cd l = cmul(A[i][k], rc);
+#pragma unroll UNR
+        for (int q = k + 1; q < n; q++) A[i][q] = cfms(l, A[k][q], A[i][q]);
+      }
+    }
+  }
+  if (zero) return make_double2(0.0, 0.0);
+  return parity ? cneg(det) : det;
+}
+
+}  // namespace dev
+}  // namespace mhc

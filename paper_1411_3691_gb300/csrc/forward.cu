@@ -1,0 +1,66 @@
+// forward.cu -- host launchers of the forward correlator and the deterministic reduction
+// of the per-work-item partial sums.
+#include "kernels.cuh"
+
+namespace mhc {
+
+namespace {
+
+// Sum of the per-item partials in a fixed order (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) reduce_kernel(const double2* __restrict__ partials,
+                                                      int64_t n, double* out) {
+  __shared__ double2 red[32];
+  double2 s = make_double2(0.0, 0.0);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    s.x += partials[i].x;
+    s.y += partials[i].y;
+  }
+  s = dev::warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      t.x += red[w].x;
+      t.y += red[w].y;
+    }
+    out[0] = t.x;
+    out[1] = t.y;
+  }
+}
+
+}  // namespace
+
+size_t forward_smem_bytes(int slots, int tile) {
+  const size_t cache = (size_t)slots * tile * sizeof(double2);
+  const size_t queue = (size_t)(tile / 32) * kQueueCap * kQueueEntryBytes;
+  return cache + queue;
+}
+
+cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t items, size_t smem,
+                           double* out, cudaStream_t s) {
+  cudaError_t e;
+  if (ncmax <= 8)
+    e = launch_fwd_nc8(a, tile, items, smem, s);
+  else if (ncmax <= 18)
+    e = launch_fwd_nc18(a, tile, items, smem, s);
+  else
+    e = launch_fwd_nc32(a, tile, items, smem, s);
+  if (e != cudaSuccess) return e;
+  return launch_reduce(a.partials, items, out, s);
+}
+
+cudaError_t launch_reduce(const double2* partials, int64_t items, double* out, cudaStream_t s) {
+  reduce_kernel<<<1, 1024, 0, s>>>(partials, items, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(const FwdArgs& a, int ncmax, int64_t n_pairs, int64_t n_src,
+                         const int64_t* ii, const int64_t* jj, const int32_t* src_member,
+                         const int32_t* mem_family, double* dets, int32_t* path, cudaStream_t s) {
+  if (ncmax <= 8) return launch_pairs_nc8(a, n_pairs, n_src, ii, jj, src_member, mem_family, dets, path, s);
+  if (ncmax <= 18) return launch_pairs_nc18(a, n_pairs, n_src, ii, jj, src_member, mem_family, dets, path, s);
+  return launch_pairs_nc32(a, n_pairs, n_src, ii, jj, src_member, mem_family, dets, path, s);
+}
+
+}  // namespace mhc

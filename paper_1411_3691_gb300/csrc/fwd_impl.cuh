@@ -1,0 +1,243 @@
+// fwd_impl.cuh -- forward correlator kernel and per-pair probe (templates; instantiated
+// once per n class by fwd_nc8.cu, fwd_nc18.cu and fwd_nc32.cu).
+//
+// One thread block per work item (work family W, tile of `tile` sinks); one thread per
+// sink.  Per flavour a thread factorises the family's shared rows against its sink's
+// columns (shared_rows) and caches y = det(G) G^{-1} e_r in shared memory; then every
+// member of the family costs one O(n) dot product per flavour (member_det), Sec. 2.1.
+// Members whose lemma factor or whose family pivots fail the guards go to a per-warp
+// queue and are refactored from scratch 32 at a time, one per lane, so the FP64 pipe
+// stays fully occupied.  Thread sums are reduced in a fixed order into one partial per
+// work item (and by reduce_kernel into C): bitwise reproducible.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mhc {
+
+namespace fwd {
+
+struct QEntry {
+  int32_t member;  // member slot
+  int32_t lane;    // lane (sink) of the warp that produced it
+  int32_t fail;    // flavours to refactor (bit f)
+  int32_t pad;
+  double2 prod;    // product of the flavours that did not fail
+};
+
+template <int NCMAX>
+__device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
+                              double2& acc) {
+  const int lane = threadIdx.x & 31;
+  if (lane < count) {
+    const QEntry e = q[lane];
+    const int64_t j = jbase + e.lane;
+    double2 prod = e.prod;
+    int32_t rows[NCMAX];
+    for (int f = 0; f < a.F; f++) {
+      if (!((e.fail >> f) & 1)) continue;
+      const int n = a.n_f[f];
+      const int rho = a.fam_rank[(int64_t)W * a.F + f];
+      dev::member_rows(a, W, e.member, f, rho, rows);
+      const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows,
+                                                   a.snk_lab + j * a.Tn + a.off_f[f]);
+      prod = dev::cmul(prod, d);
+    }
+    const int32_t sgn = a.mem_par[e.member];
+    double w = a.w_src[a.mem_term[e.member]] * a.w_snk[j];
+    if (__popc(sgn) & 1) w = -w;
+    acc.x = fma(w, prod.x, acc.x);
+    acc.y = fma(w, prod.y, acc.y);
+  }
+}
+
+template <int NCMAX>
+__global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
+  extern __shared__ double2 smem[];
+  const int T = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t item = blockIdx.x;
+  const int W = (int)(item / a.n_tiles);
+  const int tile = (int)(item % a.n_tiles);
+  const int64_t jraw = (int64_t)tile * T + tid;
+  const bool valid = jraw < a.n_snk;
+  const int64_t j = valid ? jraw : a.n_snk - 1;
+  const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
+  QEntry* queue = reinterpret_cast<QEntry*>(smem + (size_t)a.slots * T) + warp * kQueueCap;
+  double2* Y = smem + tid;
+
+  // ---- per flavour: factorise the shared rows against this sink ----------------------
+  unsigned pguard = 0;
+  int ey[MHC_FMAX];
+  for (int f = 0; f < a.F; f++) {
+    const int n = a.n_f[f];
+    ey[f] = 0;
+    if (n == 0) continue;
+    const int rho = a.fam_rank[(int64_t)W * a.F + f];
+    const bool g = dev::dispatch_shared<NCMAX>(
+        n, rho, a.S[f], a.L_f[f], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
+        a.snk_lab + j * a.Tn + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, &ey[f], a.kp);
+    pguard |= (unsigned)g << f;
+  }
+
+  // ---- per member: one dot product per flavour --------------------------------------
+  const double wj = valid ? a.w_snk[j] : 0.0;
+  double2 acc = make_double2(0.0, 0.0);
+  int qn = 0;
+  unsigned long long n_parent = 0, n_child = 0;
+  for (int c = 0; c < kW; c++) {
+    const int m = mem0 + c;
+    unsigned fail = pguard;
+    double2 prod = make_double2(1.0, 0.0);
+    bool first = true;
+    for (int f = 0; f < a.F; f++) {
+      const int n = a.n_f[f];
+      if (n == 0 || ((pguard >> f) & 1)) continue;
+      const int rho = a.fam_rank[(int64_t)W * a.F + f];
+      bool cf = false;
+      const double2 d = dev::dispatch_member<NCMAX>(
+          n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
+          a.snk_lab + j * a.Tn + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, ey[f], a.kc, &cf);
+      if (cf) {
+        fail |= 1u << f;
+      } else {
+        prod = first ? d : dev::cmul(prod, d);
+        first = false;
+      }
+    }
+    const bool need = valid && fail != 0;
+    if (!fail) {
+      double w = a.w_src[a.mem_term[m]] * wj;
+      if (__popc(a.mem_par[m]) & 1) w = -w;
+      acc.x = fma(w, prod.x, acc.x);
+      acc.y = fma(w, prod.y, acc.y);
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, need);
+    if (ball) {
+      if (need) {
+        const int pos = qn + __popc(ball & ((1u << lane) - 1u));
+        QEntry e;
+        e.member = m;
+        e.lane = lane;
+        e.fail = (int32_t)fail;
+        e.pad = 0;
+        e.prod = prod;
+        queue[pos] = e;
+        n_parent += __popc(fail & pguard);
+        n_child += __popc(fail & ~pguard);
+      }
+      qn += __popc(ball);
+      __syncwarp();
+      if (qn >= 32) {
+        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, acc);
+        __syncwarp();
+        if (lane < qn - 32) queue[lane] = queue[32 + lane];
+        __syncwarp();
+        qn -= 32;
+      }
+    }
+  }
+  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, acc);
+
+  // ---- fixed-order reduction: lanes, then warps --------------------------------------
+  acc = dev::warp_sum(acc);
+  for (int o = 16; o > 0; o >>= 1) {
+    n_parent += __shfl_xor_sync(0xffffffffu, n_parent, o);
+    n_child += __shfl_xor_sync(0xffffffffu, n_child, o);
+  }
+  __syncthreads();
+  double2* red = smem;  // reuse: the factor cache is no longer needed
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double2 s = red[0];
+    for (int w = 1; w < (T >> 5); w++) {
+      s.x += red[w].x;
+      s.y += red[w].y;
+    }
+    a.partials[item] = s;
+    if (!dev::finite2(s)) atomicOr(&a.counters[0], kStatusNonFinite);
+  }
+  if (lane == 0 && (n_parent | n_child)) {
+    atomicAdd(&a.counters[1], n_parent);
+    atomicAdd(&a.counters[2], n_child);
+  }
+}
+
+// Per-pair determinants through the same update path (one thread per pair).
+template <int NCMAX>
+__global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pairs, int64_t n_src,
+                                                  const int64_t* __restrict__ ii,
+                                                  const int64_t* __restrict__ jj,
+                                                  const int32_t* __restrict__ src_member,
+                                                  const int32_t* __restrict__ mem_family,
+                                                  double2* __restrict__ dets, int32_t* path) {
+  extern __shared__ double2 smem[];
+  const int T = blockDim.x;
+  const int64_t p = (int64_t)blockIdx.x * T + threadIdx.x;
+  if (p >= n_pairs) return;
+  const int64_t i = ii[p], j = jj[p];
+  if (i < 0 || i >= n_src || j < 0 || j >= a.n_snk) {
+    atomicOr(&a.counters[0], kStatusBadIndex);
+    return;
+  }
+  const int m = src_member[i];
+  const int W = mem_family[m];
+  double2* Y = smem + threadIdx.x;
+  int32_t rows[NCMAX];
+  int32_t bits = 0;
+  for (int f = 0; f < a.F; f++) {
+    const int n = a.n_f[f];
+    double2 d = make_double2(1.0, 0.0);
+    if (n > 0) {
+      const int rho = a.fam_rank[(int64_t)W * a.F + f];
+      const int32_t* col = a.snk_lab + j * a.Tn + a.off_f[f];
+      int ey = 0;
+      bool fail = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f],
+                                              a.fam_arow + (int64_t)W * a.Tn + a.off_f[f], col,
+                                              Y, T, &ey, a.kp);
+      if (!fail) {
+        d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f],
+                                        a.mem_lab + ((int64_t)m * a.F + f) * 2, col, Y, T, ey,
+                                        a.kc, &fail);
+      }
+      if (fail) {
+        dev::member_rows(a, W, m, f, rho, rows);
+        d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, col);
+        bits |= 1 << f;
+      }
+      if ((a.mem_par[m] >> f) & 1) d = dev::cneg(d);
+    }
+    dets[p * a.F + f] = d;
+  }
+  if (path) path[p] = bits;
+}
+
+}  // namespace fwd
+
+template <int NCMAX>
+cudaError_t launch_fwd_nc(const FwdArgs& a, int tile, int64_t items, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(fwd::fwd_kernel<NCMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fwd::fwd_kernel<NCMAX><<<(unsigned)items, tile, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NCMAX>
+cudaError_t launch_pairs_nc(const FwdArgs& a, int64_t n_pairs, int64_t n_src, const int64_t* ii,
+                            const int64_t* jj, const int32_t* src_member, const int32_t* mem_family,
+                            double* dets, int32_t* path, cudaStream_t s) {
+  const int T = 64;
+  const size_t smem = (size_t)a.slots * T * sizeof(double2);
+  if (n_pairs == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fwd::pair_kernel<NCMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((n_pairs + T - 1) / T);
+  fwd::pair_kernel<NCMAX><<<grid, T, smem, s>>>(a, n_pairs, n_src, ii, jj, src_member, mem_family,
+                                                reinterpret_cast<double2*>(dets), path);
+  return cudaGetLastError();
+}
+
+}  // namespace mhc

@@ -1,0 +1,160 @@
+// kernels.cuh -- argument blocks and dispatch shared by the forward, pair-probe, batched
+// and adjoint kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mhc.h"
+#include "device.cuh"
+
+namespace mhc {
+
+// status bits of the device status word (counters[0])
+enum : unsigned long long {
+  kStatusNonFinite = 1ull,
+  kStatusBadIndex = 2ull,
+  kStatusTimeout = 4ull,
+};
+
+// Everything one forward evaluation of one plan needs on the device.
+struct FwdArgs {
+  int F, Tn, n_tiles, slots, kp, kc;
+  int64_t n_snk;
+  int n_f[MHC_FMAX], L_f[MHC_FMAX], off_f[MHC_FMAX], yoff[MHC_FMAX];
+  const double2* S[MHC_FMAX];
+  const int32_t* fam_info;   // [W][4]: member offset, member count
+  const int32_t* fam_rank;   // [W][F]
+  const int32_t* fam_arow;   // [W][Tn]
+  const int32_t* mem_term;   // [members]
+  const int32_t* mem_par;    // [members] bit f = sign parity of flavour f
+  const int32_t* mem_lab;    // [members][F][2]
+  const int32_t* snk_lab;    // [n_snk][Tn]
+  const double* w_src;
+  const double* w_snk;
+  double2* partials;         // [items]
+  unsigned long long* counters;
+};
+
+namespace dev {
+
+// Per-(n, rank) dispatch to the register-resident specialisations (n <= 6) or the generic
+// runtime-n routine with arrays sized for the n class NCMAX.
+template <int NCMAX>
+__device__ __forceinline__ bool dispatch_shared(int n, int rho, const cd* S, int L,
+                                                const int32_t* arow, const int32_t* col, cd* Y,
+                                                int ys, int* ey, int kp) {
+#define MHC_SR(N)                                                                   \
+  case N:                                                                           \
+    return rho == 1 ? shared_rows<N, N, 1>(S, L, N, arow, col, Y, ys, ey, kp)       \
+                    : shared_rows<N, N, (N >= 2 ? 2 : 1)>(S, L, N, arow, col, Y, ys, ey, kp);
+  switch (n) {
+    MHC_SR(1)
+    MHC_SR(2)
+    MHC_SR(3)
+    MHC_SR(4)
+    MHC_SR(5)
+    MHC_SR(6)
+    default:
+      break;
+  }
+#undef MHC_SR
+  return rho == 1 ? shared_rows<NCMAX, 0, 1>(S, L, n, arow, col, Y, ys, ey, kp)
+                  : shared_rows<NCMAX, 0, 2>(S, L, n, arow, col, Y, ys, ey, kp);
+}
+
+template <int NCMAX>
+__device__ __forceinline__ cd dispatch_member(int n, int rho, const cd* S, int L,
+                                              const int32_t* lab, const int32_t* col,
+                                              const cd* Y, int ys, int ey, int kc, bool* fail) {
+#define MHC_MD(N)                                                                      \
+  case N:                                                                              \
+    return rho == 1 ? member_det<N, N, 1>(S, L, N, lab, col, Y, ys, ey, kc, fail)      \
+                    : member_det<N, N, (N >= 2 ? 2 : 1)>(S, L, N, lab, col, Y, ys, ey, kc, fail);
+  switch (n) {
+    MHC_MD(1)
+    MHC_MD(2)
+    MHC_MD(3)
+    MHC_MD(4)
+    MHC_MD(5)
+    MHC_MD(6)
+    default:
+      break;
+  }
+#undef MHC_MD
+  return rho == 1 ? member_det<NCMAX, 0, 1>(S, L, n, lab, col, Y, ys, ey, kc, fail)
+                  : member_det<NCMAX, 0, 2>(S, L, n, lab, col, Y, ys, ey, kc, fail);
+}
+
+template <int NCMAX>
+__device__ __forceinline__ cd dispatch_fresh(int n, const cd* S, int L, const int32_t* rows,
+                                             const int32_t* col) {
+#define MHC_FD(N) \
+  case N:         \
+    return fresh_det<N, N>(S, L, N, rows, col);
+  switch (n) {
+    MHC_FD(1)
+    MHC_FD(2)
+    MHC_FD(3)
+    MHC_FD(4)
+    MHC_FD(5)
+    MHC_FD(6)
+    default:
+      break;
+  }
+#undef MHC_FD
+  return fresh_det<NCMAX, 0>(S, L, n, rows, col);
+}
+
+// Rows of member m in flavour f for a fresh factorisation: the shared rows, then the
+// member's labels at the changed rows (the same order as the cached path).
+__device__ __forceinline__ void member_rows(const FwdArgs& a, int W, int m, int f, int rho,
+                                           int32_t* rows) {
+  const int n = a.n_f[f];
+  const int32_t* ar = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+  for (int i = 0; i < n - rho; i++) rows[i] = ar[i];
+  for (int t = 0; t < rho; t++) rows[n - rho + t] = a.mem_lab[((int64_t)m * a.F + f) * 2 + t];
+}
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ bool finite2(double2 v) {
+  // exponent field all ones means Inf or NaN
+  return ((__double2hiint(v.x) & 0x7ff00000) != 0x7ff00000) &&
+         ((__double2hiint(v.y) & 0x7ff00000) != 0x7ff00000);
+}
+
+}  // namespace dev
+
+// per-warp refactor queue of the forward kernel
+constexpr int kQueueCap = 64;         // entries per warp
+constexpr int kQueueEntryBytes = 32;  // sizeof(fwd::QEntry)
+
+// host-side launchers (forward.cu and fwd_nc*.cu)
+cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t items, size_t smem,
+                           double* out, cudaStream_t s);
+cudaError_t launch_reduce(const double2* partials, int64_t items, double* out, cudaStream_t s);
+cudaError_t launch_pairs(const FwdArgs& a, int ncmax, int64_t n_pairs, int64_t n_src,
+                         const int64_t* ii, const int64_t* jj, const int32_t* src_member,
+                         const int32_t* mem_family, double* dets, int32_t* path, cudaStream_t s);
+size_t forward_smem_bytes(int slots, int tile);
+#define MHC_DECL_NC(NC)                                                                       \
+  cudaError_t launch_fwd_nc##NC(const FwdArgs& a, int tile, int64_t items, size_t smem,       \
+                                cudaStream_t s);                                              \
+  cudaError_t launch_pairs_nc##NC(const FwdArgs& a, int64_t n_pairs, int64_t n_src,           \
+                                  const int64_t* ii, const int64_t* jj,                       \
+                                  const int32_t* src_member, const int32_t* mem_family,       \
+                                  double* dets, int32_t* path, cudaStream_t s);
+MHC_DECL_NC(8)
+MHC_DECL_NC(18)
+MHC_DECL_NC(32)
+#undef MHC_DECL_NC
+
+}  // namespace mhc

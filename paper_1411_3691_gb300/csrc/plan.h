@@ -1,0 +1,88 @@
+// plan.h -- host-side plan of the correlator library (internal header).
+//
+// A plan is the output of the execution-order step of the method (Sec. 3): the source
+// terms grouped into work families.  A work family has, per flavour f, a reference label
+// tuple (the dominator's, Sec. 3 greedy dominating set) and a set R_f of one or two
+// "changed rows": every member agrees with the reference on the other rows (after
+// alignment) and differs only at R_f.  Per (family, sink, flavour) the device factorises
+// the shared rows once and evaluates every member with an O(n) dot product (Sec. 2.1).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mhc.h"
+
+namespace mhc {
+
+void set_error(const std::string& msg);
+
+// Device-side tables of one plan (owned by the plan, allocated on first use).
+struct DevicePlan {
+  int device = -1;
+  int32_t* fam_info = nullptr;   // [W][4]: member offset, member count, pad, pad
+  int32_t* fam_rank = nullptr;   // [W][F]
+  int32_t* fam_arow = nullptr;   // [W][Tn]: shared-row labels first, then unused
+  int32_t* mem_term = nullptr;   // [n_src] source term index of each member
+  int32_t* mem_par = nullptr;    // [n_src] bit f: sign parity of flavour f
+  int32_t* mem_lab = nullptr;    // [n_src][F][2]
+  int32_t* snk_lab = nullptr;    // [n_snk][Tn]
+  int32_t* src_member = nullptr; // [n_src] member slot of each source term
+  int32_t* mem_family = nullptr; // [n_src] family of each member slot
+  double* w_src = nullptr;       // [n_src] plan weights
+  double* w_snk = nullptr;       // [n_snk]
+  double* partials = nullptr;    // [items][2] per-work-item partial sums
+  unsigned long long* counters = nullptr;  // [4]: status bits, refactor parent, child, spare
+  int64_t n_items = 0;
+  int32_t n_tiles = 0;           // sink tiles per family
+  int32_t tile = 0;              // sinks per tile (threads per block)
+  // backward workspace (lazy)
+  double* bwd_rows = nullptr;    // per (family, chunk) row accumulators
+  size_t bwd_rows_bytes = 0;
+  double* bwd_wsrc = nullptr;    // [n_src][2] complex dC/dw_src partial sums per sink chunk
+  size_t bwd_wsrc_bytes = 0;
+  double* bwd_wsnk = nullptr;    // [n_snk][2] per family-chunk partials
+  size_t bwd_wsnk_bytes = 0;
+};
+
+struct Plan {
+  // inputs (host copies)
+  int F = 0;
+  std::vector<int32_t> n_f, L_f, off_f;  // off_f: label offset of flavour f inside a term
+  int Tn = 0;                            // sum n_f
+  int64_t n_src = 0, n_snk = 0;
+  std::vector<int32_t> labels_src, labels_snk;
+  std::vector<double> w_src, w_snk;
+  mhc_plan_opts opts{};
+  // work families
+  int64_t n_fam = 0;
+  std::vector<int64_t> fam_off;          // [W+1]
+  std::vector<int32_t> fam_rank;         // [W][F]
+  std::vector<int32_t> fam_rows;         // [W][F][2]
+  std::vector<int32_t> fam_ref;          // [W][Tn]
+  std::vector<int32_t> fam_arow;         // [W][Tn]
+  std::vector<int64_t> mem_term;         // [n_src]
+  std::vector<int32_t> mem_sign;         // [n_src] +-1 (product over flavours)
+  std::vector<int32_t> mem_par;          // [n_src] bit f: sign parity of flavour f
+  std::vector<int32_t> mem_lab;          // [n_src][F][2]
+  std::vector<int32_t> src_member;       // [n_src] member slot of each source term
+  std::vector<int32_t> mem_family;       // [n_src]
+  int max_members = 0;
+  int max_n = 0;
+  // stats
+  mhc_stats stats{};
+  // device state
+  DevicePlan dev;
+};
+
+// Builds every host table of `p` from its inputs; returns MHC_OK or sets the error.
+mhc_status build_plan(Plan& p);
+
+// Algorithmic flop counts (counting rule: real add/mul 1, fma 2, complex mul 6,
+// complex fma 8, complex reciprocal 6, pivot measure |re|+|im| 1).
+double flops_shared_rows(int n, int rho);   // factorise + solve for one (family, sink, flavour)
+double flops_member(int n, int rho);        // one member's det from the cached solve
+double flops_fresh_lu(int n);               // one fresh partial-pivot LU determinant
+
+}  // namespace mhc

@@ -1,0 +1,556 @@
+// planner.cpp -- host planner: validation, source-term graph, greedy dominating set,
+// member alignment and work families (Sec. 3 of the paper: execution order).
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "plan.h"
+
+namespace mhc {
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Largest bucket of the candidate-pair hash scan that is compared exhaustively; pairs of
+// a longer bucket are compared only within a sliding window of this many terms.
+constexpr size_t kBucketWindow = 2048;
+// Rank-2 adjacency is used for a flavour only when n_f is at least this large: below
+// it two shared rows out of n_f leave too little to share.
+constexpr int kRank2MinN = 6;
+
+uint64_t mix64(uint64_t x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ULL;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebULL;
+  x ^= x >> 31;
+  return x;
+}
+
+// number of labels two sorted multisets share
+int common_sorted(const int32_t* a, const int32_t* b, int n) {
+  int i = 0, j = 0, c = 0;
+  while (i < n && j < n) {
+    if (a[i] == b[j]) {
+      c++;
+      i++;
+      j++;
+    } else if (a[i] < b[j]) {
+      i++;
+    } else {
+      j++;
+    }
+  }
+  return c;
+}
+
+int perm_parity(const std::vector<int>& p) {
+  int inv = 0;
+  for (size_t a = 0; a < p.size(); a++)
+    for (size_t b = a + 1; b < p.size(); b++)
+      if (p[a] > p[b]) inv++;
+  return inv & 1;
+}
+
+// Alignment of one member tuple t to the reference tuple ref (both n labels, given order).
+struct Align {
+  std::vector<int> changed;  // reference positions not matched (ascending)
+  std::vector<int> aligned;  // member labels placed at the reference positions
+  int parity = 0;            // parity of the row permutation: det(t) = (-1)^parity det(aligned)
+};
+
+Align align(const int32_t* ref, const int32_t* t, int n) {
+  Align a;
+  std::vector<int> match(n, -1);  // ref position -> member position
+  std::vector<char> used(n, 0);
+  for (int m = 0; m < n; m++)
+    for (int p = 0; p < n; p++)
+      if (!used[p] && t[p] == ref[m]) {
+        match[m] = p;
+        used[p] = 1;
+        break;
+      }
+  std::vector<int> extras;  // member positions not matched (ascending)
+  for (int p = 0; p < n; p++)
+    if (!used[p]) extras.push_back(p);
+  a.aligned.assign(ref, ref + n);
+  std::vector<int> pi(n, -1);  // member position -> aligned position
+  int k = 0;
+  for (int m = 0; m < n; m++) {
+    if (match[m] >= 0) {
+      pi[match[m]] = m;
+    } else {
+      a.changed.push_back(m);
+      a.aligned[m] = t[extras[k]];
+      pi[extras[k]] = m;
+      k++;
+    }
+  }
+  a.parity = perm_parity(pi);
+  return a;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+double flops_shared_rows(int n, int rho) {
+  const double M = n - rho;
+  if (n <= 0) return 0.0;
+  double f = 0.0;
+  f += M * (M + 1) / 2;                        // pivot measures |re|+|im|
+  f += 6.0 * M;                                // pivot reciprocals
+  f += 6.0 * M * (M - 1) / 2;                  // multipliers
+  double upd = 0.0;
+  for (int k = 0; k < (int)M; k++) upd += (M - 1 - k) * (n - 1 - k);
+  f += 8.0 * upd;                              // trailing updates
+  if (M >= 1) f += 6.0 * (M - 1);              // det of the shared-row factor
+  f += rho * (8.0 * M * (M - 1) / 2 + 6.0 * M);  // back substitutions
+  f += rho * 6.0 * M;                          // scaling by the determinant
+  return f;
+}
+
+double flops_member(int n, int rho) {
+  if (n <= 0) return 0.0;
+  const double dot = 6.0 + 8.0 * (n - 1);
+  return rho == 2 ? 4.0 * dot + 2.0 * 6.0 + 2.0 : dot;
+}
+
+double flops_fresh_lu(int n) {
+  if (n <= 0) return 0.0;
+  double f = n * (n + 1) / 2.0;                  // pivot measures
+  f += 6.0 * (n - 1);                            // reciprocals
+  f += 6.0 * n * (n - 1) / 2.0;                  // multipliers
+  f += 8.0 * (n - 1) * n * (2.0 * n - 1) / 6.0;  // trailing updates
+  f += 6.0 * (n - 1);                            // product of the pivots
+  return f;
+}
+
+mhc_status build_plan(Plan& p) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int F = p.F;
+  const int64_t N = p.n_src;
+  const int Tn = p.Tn;
+  const int rank2 = p.opts.rank2 ? 1 : 0;
+  const int kmax = p.opts.max_family;
+
+  // ---- per term, per flavour sorted label multisets -------------------------------
+  std::vector<int32_t> sorted(p.labels_src);
+  for (int64_t i = 0; i < N; i++)
+    for (int f = 0; f < F; f++)
+      std::sort(sorted.begin() + i * Tn + p.off_f[f], sorted.begin() + i * Tn + p.off_f[f] + p.n_f[f]);
+  std::vector<int> dmax(F);
+  for (int f = 0; f < F; f++) dmax[f] = (rank2 && p.n_f[f] >= kRank2MinN) ? 2 : 1;
+
+  // key flavour: the smallest allowed difference, then the largest n
+  int f0 = -1;
+  for (int f = 0; f < F; f++) {
+    if (p.n_f[f] == 0) continue;
+    if (f0 < 0 || dmax[f] < dmax[f0] || (dmax[f] == dmax[f0] && p.n_f[f] > p.n_f[f0])) f0 = f;
+  }
+
+  // ---- candidate pairs: shared leave-d-out keys of the key flavour ------------------
+  std::vector<std::pair<uint64_t, int32_t>> keys;
+  if (f0 >= 0) {
+    const int n = p.n_f[f0], d = std::min(dmax[f0], n);
+    keys.reserve((size_t)N * (d == 1 ? n : n * (n - 1) / 2 + 1));
+    std::vector<int32_t> rest;
+    for (int64_t i = 0; i < N; i++) {
+      const int32_t* s = &sorted[i * Tn + p.off_f[f0]];
+      auto emit = [&](int skip1, int skip2) {
+        uint64_t h = 0x9e3779b97f4a7c15ULL;
+        for (int m = 0; m < n; m++)
+          if (m != skip1 && m != skip2) h = mix64(h ^ (uint64_t)(uint32_t)s[m]);
+        keys.emplace_back(h, (int32_t)i);
+      };
+      if (d == 1) {
+        for (int m = 0; m < n; m++)
+          if (m == 0 || s[m] != s[m - 1]) emit(m, -1);
+      } else if (n == 2) {
+        emit(0, 1);
+      } else {
+        for (int m1 = 0; m1 < n; m1++)
+          for (int m2 = m1 + 1; m2 < n; m2++) emit(m1, m2);
+      }
+    }
+  } else {
+    for (int64_t i = 0; i < N; i++) keys.emplace_back(0, (int32_t)i);
+  }
+  std::sort(keys.begin(), keys.end());
+  std::vector<std::pair<int32_t, int32_t>> cand;
+  for (size_t a = 0; a < keys.size();) {
+    size_t b = a;
+    while (b < keys.size() && keys[b].first == keys[a].first) b++;
+    for (size_t x = a; x < b; x++)
+      for (size_t y = x + 1; y < b && y - x < kBucketWindow; y++)
+        if (keys[x].second != keys[y].second) cand.emplace_back(keys[x].second, keys[y].second);
+    a = b;
+  }
+  keys.clear();
+  keys.shrink_to_fit();
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+
+  // ---- exact adjacency check: every flavour differs in at most dmax[f] labels ---------
+  std::vector<std::vector<int32_t>> adj(N);
+  int64_t edges = 0;
+  for (auto& e : cand) {
+    const int64_t i = e.first, j = e.second;
+    bool ok = true;
+    for (int f = 0; f < F && ok; f++) {
+      const int n = p.n_f[f];
+      if (n == 0) continue;
+      const int c = common_sorted(&sorted[i * Tn + p.off_f[f]], &sorted[j * Tn + p.off_f[f]], n);
+      ok = (n - c) <= dmax[f];
+    }
+    if (ok) {
+      adj[i].push_back((int32_t)j);
+      adj[j].push_back((int32_t)i);
+      edges++;
+    }
+  }
+  cand.clear();
+  cand.shrink_to_fit();
+  for (auto& a : adj) std::sort(a.begin(), a.end());
+
+  // ---- greedy dominating set (Sec. 3): highest remaining degree, ties to lowest index -
+  std::vector<int32_t> deg(N);
+  std::vector<char> alive(N, 1);
+  std::set<std::pair<int32_t, int32_t>> pq;  // (-degree, index)
+  for (int64_t i = 0; i < N; i++) {
+    deg[i] = (int32_t)adj[i].size();
+    pq.emplace(-deg[i], (int32_t)i);
+  }
+  std::vector<std::vector<int32_t>> dom_sets;  // dominator first, then its neighbours
+  while (!pq.empty()) {
+    const int32_t v = pq.begin()->second;
+    std::vector<int32_t> fam{v};
+    for (int32_t u : adj[v])
+      if (alive[u]) fam.push_back(u);
+    for (int32_t x : fam) {
+      pq.erase({-deg[x], x});
+      alive[x] = 0;
+    }
+    for (int32_t x : fam)
+      for (int32_t w : adj[x])
+        if (alive[w]) {
+          pq.erase({-deg[w], w});
+          deg[w]--;
+          pq.emplace(-deg[w], w);
+        }
+    std::sort(fam.begin() + 1, fam.end());
+    dom_sets.push_back(std::move(fam));
+  }
+  adj.clear();
+
+  // ---- work families: align members, group by compatible changed rows ---------------
+  p.fam_off.assign(1, 0);
+  p.fam_rank.clear();
+  p.fam_rows.clear();
+  p.fam_ref.clear();
+  p.fam_arow.clear();
+  p.mem_term.clear();
+  p.mem_sign.clear();
+  p.mem_par.clear();
+  p.mem_lab.clear();
+  p.src_member.assign(N, -1);
+  p.mem_family.clear();
+  int64_t rank2_blocks = 0;
+  p.max_members = 0;
+
+  struct Member {
+    int32_t term;
+    std::vector<Align> al;  // per flavour
+  };
+  struct Group {
+    std::vector<std::vector<int>> R;  // per flavour, ascending changed rows
+    std::vector<int> members;         // indices into the member list
+  };
+  for (auto& ds : dom_sets) {
+    const int32_t v = ds[0];
+    const int32_t* ref = &p.labels_src[(int64_t)v * Tn];
+    std::vector<Member> mems;
+    for (int32_t t : ds) {
+      Member m;
+      m.term = t;
+      for (int f = 0; f < F; f++)
+        m.al.push_back(align(ref + p.off_f[f], &p.labels_src[(int64_t)t * Tn + p.off_f[f]], p.n_f[f]));
+      mems.push_back(std::move(m));
+    }
+    std::vector<Group> groups;
+    for (int mi = 0; mi < (int)mems.size(); mi++) {
+      bool placed = false;
+      for (auto& g : groups) {
+        if ((int)g.members.size() >= kmax) continue;
+        bool ok = true;
+        std::vector<std::vector<int>> U(F);
+        for (int f = 0; f < F && ok; f++) {
+          std::set<int> u(g.R[f].begin(), g.R[f].end());
+          u.insert(mems[mi].al[f].changed.begin(), mems[mi].al[f].changed.end());
+          U[f].assign(u.begin(), u.end());
+          ok = (int)U[f].size() <= dmax[f];
+        }
+        if (ok) {
+          g.R = U;
+          g.members.push_back(mi);
+          placed = true;
+          break;
+        }
+      }
+      if (!placed) {
+        Group g;
+        g.R.resize(F);
+        for (int f = 0; f < F; f++) g.R[f] = mems[mi].al[f].changed;
+        g.members.push_back(mi);
+        groups.push_back(std::move(g));
+      }
+    }
+    for (auto& g : groups) {
+      const int64_t W = p.n_fam++;
+      std::vector<int32_t> ranks(F), rows(2 * F, -1), arow(Tn, -1);
+      std::vector<int> eps(F, 0);
+      for (int f = 0; f < F; f++) {
+        const int n = p.n_f[f];
+        std::vector<int> R = g.R[f];
+        if (n == 0) {
+          ranks[f] = 0;
+          continue;
+        }
+        if (R.empty()) R.push_back(n - 1);
+        ranks[f] = (int32_t)R.size();
+        if (R.size() == 2) rank2_blocks++;
+        for (size_t k = 0; k < R.size(); k++) rows[2 * f + k] = R[k];
+        // [shared rows ascending; changed rows ascending] and the sign of that reordering
+        std::vector<int> order;
+        int a = 0;
+        for (int m = 0; m < n; m++)
+          if (std::find(R.begin(), R.end(), m) == R.end()) {
+            order.push_back(m);
+            arow[p.off_f[f] + a++] = ref[p.off_f[f] + m];
+          }
+        for (int r : R) order.push_back(r);
+        eps[f] = perm_parity(order);
+        g.R[f] = R;
+      }
+      for (int f = 0; f < F; f++) p.fam_rank.push_back(ranks[f]);
+      p.fam_rows.insert(p.fam_rows.end(), rows.begin(), rows.end());
+      p.fam_ref.insert(p.fam_ref.end(), ref, ref + Tn);
+      p.fam_arow.insert(p.fam_arow.end(), arow.begin(), arow.end());
+      for (int mi : g.members) {
+        const Member& m = mems[mi];
+        int parity = 0, bits = 0;
+        std::vector<int32_t> lab(2 * F, -1);
+        for (int f = 0; f < F; f++) {
+          if (p.n_f[f] == 0) continue;
+          const int pf = m.al[f].parity ^ eps[f];
+          parity ^= pf;
+          bits |= pf << f;
+          for (int k = 0; k < ranks[f]; k++) lab[2 * f + k] = m.al[f].aligned[g.R[f][k]];
+        }
+        p.mem_lab.insert(p.mem_lab.end(), lab.begin(), lab.end());
+        p.src_member[m.term] = (int32_t)p.mem_term.size();
+        p.mem_term.push_back(m.term);
+        p.mem_sign.push_back(parity ? -1 : 1);
+        p.mem_par.push_back(bits);
+        p.mem_family.push_back((int32_t)W);
+      }
+      p.fam_off.push_back((int64_t)p.mem_term.size());
+      p.max_members = std::max(p.max_members, (int)g.members.size());
+    }
+  }
+
+  // ---- statistics -------------------------------------------------------------------
+  mhc_stats& s = p.stats;
+  std::memset(&s, 0, sizeof(s));
+  s.n_src = p.n_src;
+  s.n_snk = p.n_snk;
+  s.n_flavours = F;
+  s.max_n = p.max_n;
+  s.dominators = (int64_t)dom_sets.size();
+  s.families = p.n_fam;
+  s.rank2_family_flavours = rank2_blocks;
+  s.members = (int64_t)p.mem_term.size();
+  s.graph_edges = edges;
+  double fl = 0.0;
+  for (int64_t W = 0; W < p.n_fam; W++) {
+    const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
+    for (int f = 0; f < F; f++) {
+      const int n = p.n_f[f], rho = p.fam_rank[W * F + f];
+      if (n == 0) continue;
+      fl += (double)p.n_snk * (flops_shared_rows(n, rho) + k * flops_member(n, rho));
+    }
+  }
+  int Fa = 0;
+  for (int f = 0; f < F; f++) Fa += p.n_f[f] > 0;
+  const double combine = 6.0 * std::max(Fa - 1, 0) + 1.0 + 4.0;  // flavour product, w_i w_j, accumulate
+  fl += combine * (double)p.n_src * (double)p.n_snk;
+  s.flops_per_call = fl;
+  double fresh = 0.0;
+  for (int f = 0; f < F; f++) fresh += flops_fresh_lu(p.n_f[f]);
+  s.fresh_lu_flops_per_pair = fresh + combine;
+  double bytes = 16.0;
+  for (int f = 0; f < F; f++) bytes += 16.0 * p.L_f[f] * p.L_f[f];
+  bytes += 4.0 * Tn * (double)(p.n_src + p.n_snk) + 8.0 * (double)(p.n_src + p.n_snk);
+  s.bytes_per_call = bytes;
+  s.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return MHC_OK;
+}
+
+}  // namespace mhc
+
+using namespace mhc;
+
+extern "C" {
+
+const char* mhc_last_error(void) { return g_last_error.c_str(); }
+
+void mhc_plan_opts_default(mhc_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tau_parent = 1e-4;
+  o->tau_child = 1e-3;
+  o->sink_tile = 0;
+  o->rank2 = 1;
+  o->max_family = 32;
+}
+
+mhc_status mhc_plan(mhc_plan_t* out, int32_t F, const int32_t* n_f, const int32_t* L_f, int64_t n_src,
+                    const int32_t* labels_src, const double* w_src, int64_t n_snk,
+                    const int32_t* labels_snk, const double* w_snk, const mhc_plan_opts* opts) {
+  if (!out) {
+    set_error("mhc_plan: out is NULL");
+    return MHC_EINVAL;
+  }
+  *out = nullptr;
+  if (F <= 0 || F > MHC_FMAX) {
+    set_error("mhc_plan: n_flavours must be in [1, " + std::to_string(MHC_FMAX) + "]");
+    return MHC_EINVAL;
+  }
+  if (!n_f || !L_f || !labels_src || !labels_snk || !w_src || !w_snk) {
+    set_error("mhc_plan: NULL input pointer");
+    return MHC_EINVAL;
+  }
+  if (n_src <= 0 || n_snk <= 0 || n_src > (int64_t)INT32_MAX || n_snk > (int64_t)INT32_MAX) {
+    set_error("mhc_plan: term counts must be in [1, 2^31)");
+    return MHC_EINVAL;
+  }
+  Plan* p = nullptr;
+  try {
+    p = new Plan();
+    p->F = F;
+    p->n_f.assign(n_f, n_f + F);
+    p->L_f.assign(L_f, L_f + F);
+    p->off_f.resize(F);
+    int Tn = 0;
+    for (int f = 0; f < F; f++) {
+      if (n_f[f] < 0 || n_f[f] > MHC_NMAX) {
+        set_error("mhc_plan: n_f[" + std::to_string(f) + "] = " + std::to_string(n_f[f]) +
+                  " outside [0, " + std::to_string(MHC_NMAX) + "]");
+        delete p;
+        return MHC_EINVAL;
+      }
+      if (L_f[f] < 1 || L_f[f] > 4096) {
+        set_error("mhc_plan: L_f[" + std::to_string(f) + "] outside [1, 4096]");
+        delete p;
+        return MHC_EINVAL;
+      }
+      p->off_f[f] = Tn;
+      Tn += n_f[f];
+      p->max_n = std::max(p->max_n, (int)n_f[f]);
+    }
+    p->Tn = Tn;
+    p->n_src = n_src;
+    p->n_snk = n_snk;
+    p->labels_src.assign(labels_src, labels_src + n_src * Tn);
+    p->labels_snk.assign(labels_snk, labels_snk + n_snk * Tn);
+    p->w_src.assign(w_src, w_src + n_src);
+    p->w_snk.assign(w_snk, w_snk + n_snk);
+    for (int side = 0; side < 2; side++) {
+      const std::vector<int32_t>& lab = side ? p->labels_snk : p->labels_src;
+      const int64_t Nn = side ? n_snk : n_src;
+      for (int64_t i = 0; i < Nn; i++)
+        for (int f = 0; f < F; f++)
+          for (int m = 0; m < n_f[f]; m++) {
+            const int32_t x = lab[i * Tn + p->off_f[f] + m];
+            if (x < 0 || x >= L_f[f]) {
+              set_error(std::string("mhc_plan: ") + (side ? "sink" : "source") + " term " +
+                        std::to_string(i) + " flavour " + std::to_string(f) + " label " +
+                        std::to_string(x) + " outside [0, L_f)");
+              delete p;
+              return MHC_EINVAL;
+            }
+          }
+    }
+    if (opts) {
+      p->opts = *opts;
+    } else {
+      mhc_plan_opts_default(&p->opts);
+    }
+    if (p->opts.max_family <= 0) p->opts.max_family = 32;
+    if (p->opts.max_family > 64) {
+      set_error("mhc_plan: max_family must be in [1, 64]");
+      delete p;
+      return MHC_EINVAL;
+    }
+    if (!(p->opts.tau_parent >= 0.0 && p->opts.tau_parent < 1.0) ||
+        !(p->opts.tau_child >= 0.0 && p->opts.tau_child < 1.0)) {
+      set_error("mhc_plan: tau_parent and tau_child must be in [0, 1)");
+      delete p;
+      return MHC_EINVAL;
+    }
+    if (p->opts.sink_tile != 0 && p->opts.sink_tile != 32 && p->opts.sink_tile != 64 &&
+        p->opts.sink_tile != 128) {
+      set_error("mhc_plan: sink_tile must be 0, 32, 64 or 128");
+      delete p;
+      return MHC_EINVAL;
+    }
+    mhc_status st = build_plan(*p);
+    if (st != MHC_OK) {
+      delete p;
+      return st;
+    }
+  } catch (const std::bad_alloc&) {
+    delete p;
+    set_error("mhc_plan: out of host memory");
+    return MHC_ENOMEM;
+  }
+  *out = reinterpret_cast<mhc_plan_t>(p);
+  return MHC_OK;
+}
+
+mhc_status mhc_plan_families(mhc_plan_t plan, int64_t* n_families, int64_t* fam_member_offset,
+                             int32_t* fam_rank, int32_t* fam_rows, int32_t* fam_ref,
+                             int64_t* member_term, int32_t* member_sign, int32_t* member_labels) {
+  if (!plan || !n_families) {
+    set_error("mhc_plan_families: NULL argument");
+    return MHC_EINVAL;
+  }
+  const Plan& p = *reinterpret_cast<const Plan*>(plan);
+  *n_families = p.n_fam;
+  if (fam_member_offset) std::copy(p.fam_off.begin(), p.fam_off.end(), fam_member_offset);
+  if (fam_rank) std::copy(p.fam_rank.begin(), p.fam_rank.end(), fam_rank);
+  if (fam_rows) std::copy(p.fam_rows.begin(), p.fam_rows.end(), fam_rows);
+  if (fam_ref) std::copy(p.fam_ref.begin(), p.fam_ref.end(), fam_ref);
+  if (member_term) std::copy(p.mem_term.begin(), p.mem_term.end(), member_term);
+  if (member_sign) std::copy(p.mem_sign.begin(), p.mem_sign.end(), member_sign);
+  if (member_labels) std::copy(p.mem_lab.begin(), p.mem_lab.end(), member_labels);
+  return MHC_OK;
+}
+
+mhc_status mhc_plan_stats(mhc_plan_t plan, mhc_stats* out) {
+  if (!plan || !out) {
+    set_error("mhc_plan_stats: NULL argument");
+    return MHC_EINVAL;
+  }
+  *out = reinterpret_cast<const Plan*>(plan)->stats;
+  return MHC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+"""GPU parity of the forward correlator and the per-pair probe against the oracle.
+
+Tolerances (from the arithmetic; stated per test):
+  * C: |C_gpu - C_oracle| <= 1e-11 * sum_ij |w_i w_j prod det|.
+  * per pair and flavour: |d_gpu - d_ref| <= 1e-12 |d_ref|, or, for an ill-conditioned
+    block, <= 4 n u kappa_inf(G) |d_ref| with d_ref in double-double and u = 2^-53.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1411_3691_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1411_3691_gb300 import build as B
+    B.build()
+    from paper_1411_3691_gb300 import mhc
+    return mhc
+
+
+def dev_S(w):
+    return [torch.from_numpy(np.ascontiguousarray(s)).cuda() for s in w.S]
+
+
+def gpu_C(M, w, opts=None, plan=None, S=None):
+    plan = plan or M.Plan.from_workload(w, opts)
+    S = S or dev_S(w)
+    out = plan.correlator(S)
+    torch.cuda.synchronize()
+    return complex(out[0].item(), out[1].item()), plan, S
+
+
+def small_cases():
+    he = wl.helium4(scale=6 / 256)
+    he.labels_snk, he.w_snk = he.labels_snk[:300], he.w_snk[:300]          # ragged sink tile
+    lg = wl.large_nucleus(scale=4 / 1024)
+    lg.labels_snk, lg.w_snk = lg.labels_snk[:70], lg.w_snk[:70]
+    rep = wl.make_workload("repeat", [4, 3], [10, 9], [6, 3, 5], [4, 4, 3], seed=44)
+    rng = np.random.default_rng(3)
+    for t in rng.choice(rep.labels_src.shape[0], 4, replace=False):
+        rep.labels_src[t, 1] = rep.labels_src[t, 0]                         # repeated label: det 0
+    diag = wl.make_workload("diag", [3, 3], [8, 8], [4, 4, 4], [6, 6], seed=45)
+    d = [np.diag(np.diag(s)) for s in diag.S]
+    diag.S = [np.ascontiguousarray(x) for x in d]
+    perm_snk = np.concatenate([diag.labels_src[:, :3][:, ::-1], diag.labels_src[:, 3:]], axis=1)
+    diag.labels_snk = np.concatenate([diag.labels_snk, perm_snk]).astype(np.int32)
+    diag.w_snk = np.concatenate([diag.w_snk, np.ones(perm_snk.shape[0])])
+    return {
+        "deuteron_full": wl.deuteron(),
+        "he4_ragged": he,
+        "large_rank2_forced": lg,
+        "mixed_nf0": wl.make_workload("mixed", [3, 0, 7], [24, 5, 30], [5, 1, 3, 8, 2], [7, 9, 3], seed=9,
+                                      two_row_frac=0.3),
+        "n9_n12": wl.make_workload("n9n12", [9, 12], [36, 48], [5, 7, 3], [40, 33], seed=10, two_row_frac=0.2),
+        "n1": wl.make_workload("n1", [1, 1], [6, 7], [3, 2, 4], [5, 4], seed=11),
+        "repeated_labels": rep,
+        "diagonal_S": diag,
+        "n32": wl.make_workload("n32", [32], [64], [3, 2], [40], seed=12),
+    }
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_matches_oracle(M, name):
+    w = CASES[name]
+    C, plan, S = gpu_C(M, w)
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (name, C, ref, abs(C - ref) / scale)
+    code = M.mhc_get_status_code(plan.handle)
+    assert code == M.MHC_OK
+    plan.close()
+
+
+def test_forward_deterministic(M):
+    w = CASES["large_rank2_forced"]
+    plan = M.Plan.from_workload(w)
+    S = dev_S(w)
+    a = plan.correlator(S).cpu().numpy()
+    b = plan.correlator(S).cpu().numpy()
+    assert a.tobytes() == b.tobytes()
+
+
+def test_weights_override(M):
+    w = CASES["he4_ragged"]
+    plan = M.Plan.from_workload(w)
+    S = dev_S(w)
+    rng = np.random.default_rng(5)
+    ws, wk = rng.normal(size=w.w_src.shape), rng.normal(size=w.w_snk.shape)
+    out = plan.correlator(S, torch.from_numpy(ws).cuda(), torch.from_numpy(wk).cuda())
+    C = complex(*out.cpu().numpy())
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, ws, w.labels_snk, wk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale
+
+
+def check_pairs(M, w, plan, S, ii, jj):
+    it = torch.from_numpy(ii.astype(np.int64)).cuda()
+    jt = torch.from_numpy(jj.astype(np.int64)).cuda()
+    path = torch.zeros(len(ii), dtype=torch.int32, device="cuda")
+    got = plan.pair_dets(S, it, jt, path).cpu().numpy()
+    path = path.cpu().numpy()
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    ref = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj)
+    off = np.cumsum([0] + w.n_f)
+    n_ill = 0
+    for p in range(len(ii)):
+        for f, n in enumerate(w.n_f):
+            if n == 0:
+                continue
+            err = abs(got[p, f] - ref[p, f])
+            if err <= 1e-12 * abs(ref[p, f]):
+                continue
+            G = w.S[f][np.ix_(w.labels_src[ii[p], off[f]:off[f] + n], w.labels_snk[jj[p], off[f]:off[f] + n])]
+            kap = oracle.cond_inf(G)
+            hr, lr, hi, li = oracle.det_dd(G)
+            dd = complex(hr + lr, hi + li)
+            n_ill += 1
+            assert abs(got[p, f] - dd) <= 4 * n * U * kap * abs(dd) + 1e-300, (p, f, got[p, f], dd, kap)
+    return path, n_ill
+
+
+def test_pair_dets(M):
+    w = CASES["large_rank2_forced"]
+    plan = M.Plan.from_workload(w)
+    S = dev_S(w)
+    ii, jj = np.meshgrid(np.arange(len(w.w_src)), np.arange(len(w.w_snk)), indexing="ij")
+    path, n_ill = check_pairs(M, w, plan, S, ii.ravel(), jj.ravel())
+    # the forced near-singular members took the refactor path for every sink
+    forced = w.meta["src"]["forced"]
+    assert len(forced) > 0
+    P = path.reshape(len(w.w_src), len(w.w_snk))
+    for t, f in forced:
+        assert np.all((P[t] >> f) & 1), (t, f)
+
+
+def test_refactor_counters(M):
+    w = CASES["large_rank2_forced"]
+    C, plan, S = gpu_C(M, w)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    st = plan.stats()
+    forced = w.meta["src"]["forced"]
+    assert st["refactor_child"] >= len(forced) * len(w.w_snk)
+
+
+def test_nonfinite_status(M):
+    w = wl.deuteron(scale=2 / 64)
+    S = dev_S(w)
+    S[0][w.labels_src[0, 0], :] = float("nan")
+    C, plan, S = gpu_C(M, w, S=S)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_ENONFINITE
+
+
+def test_full_helium4(M):
+    """The 4096 x 4096 He-4-like workload at full size against the threaded oracle."""
+    w = wl.helium4()
+    C, plan, S = gpu_C(M, w)
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=16)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+
+
+def test_full_large_nucleus_sampled(M):
+    """32768 x 32768, n = 18: 10^5 seeded pairs through the probe against the oracle (the
+    launch configuration of the full plan), and C of a 4-family sub-plan x all sinks."""
+    w = wl.large_nucleus()
+    plan = M.Plan.from_workload(w)
+    S = dev_S(w)
+    rng = np.random.default_rng(31)
+    ii = rng.integers(0, len(w.w_src), 100000)
+    jj = rng.integers(0, len(w.w_snk), 100000)
+    path, n_ill = check_pairs(M, w, plan, S, ii, jj)
+    plan.close()
+    k = 4 * 32
+    sub = wl.Workload("sub", w.n_f, w.S, w.labels_src[:k], w.w_src[:k], w.labels_snk, w.w_snk)
+    C, plan, S = gpu_C(M, sub, S=S)
+    ref, scale = oracle.correlator(sub.S, sub.n_f, sub.labels_src, sub.w_src, sub.labels_snk, sub.w_snk,
+                                   threads=16)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref)

@@ -1,0 +1,228 @@
+"""Planner (host) tests through the C ABI, on the CPU: the library loads and exports every
+declared symbol; plans cover every source term once; members are aligned to their
+family's reference tuple with the right sign; a CPU walk of the plan with the lemma
+reproduces the oracle's determinants; the greedy dominating set follows Sec. 3."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_3691_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1411_3691_gb300 import build as B
+    B.build()
+    from paper_1411_3691_gb300 import mhc
+    return mhc
+
+
+def test_exports_every_declared_symbol(M):
+    hdr = open(os.path.join(ROOT, "include", "mhc.h")).read()
+    declared = set(re.findall(r"\b(mhc_[a-z0-9_]+)\s*\(", hdr))
+    assert len(declared) >= 14
+    L = M.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), f"{name} declared in include/mhc.h but not exported"
+    assert set(M.EXPORTED) <= declared
+
+
+def _walk(M, w, plan):
+    """Evaluate every (member, sink) determinant from the plan's families: the shared rows
+    of the reference tuple plus the member's rows (LAPACK det), times the member sign."""
+    fam = plan.families()
+    F, Tn = plan.F, plan.Tn
+    off = np.cumsum([0] + w.n_f)
+    dets = np.zeros((plan.n_src, plan.n_snk), dtype=complex)
+    for W in range(len(fam["offset"]) - 1):
+        for m in range(fam["offset"][W], fam["offset"][W + 1]):
+            i = fam["term"][m]
+            val = np.ones(plan.n_snk, dtype=complex) * fam["sign"][m]
+            for f in range(F):
+                n = w.n_f[f]
+                if n == 0:
+                    continue
+                rho = fam["rank"][W, f]
+                R = [r for r in fam["rows"][W, f] if r >= 0]
+                assert len(R) == rho
+                ref = fam["ref"][W, off[f]:off[f] + n]
+                shared = [ref[q] for q in range(n) if q not in R]
+                rows = shared + list(fam["labels"][m, f, :rho])
+                for j in range(plan.n_snk):
+                    col = w.labels_snk[j, off[f]:off[f] + n]
+                    val[j] *= np.linalg.det(w.S[f][np.ix_(rows, col)])
+            dets[i] = val
+    return dets
+
+
+@pytest.mark.parametrize("name", ["deuteron", "helium4", "large", "mixed"])
+def test_plan_walk_matches_oracle(M, name):
+    if name == "deuteron":
+        w = wl.deuteron(scale=6 / 64)
+    elif name == "helium4":
+        w = wl.helium4(scale=4 / 256)
+        w.labels_snk = w.labels_snk[:24]
+        w.w_snk = w.w_snk[:24]
+    elif name == "large":
+        w = wl.make_workload("large-small", [10, 8], [40, 36], [12, 9, 7], [5, 4], diag=3.0, seed=5,
+                             two_row_frac=0.5, forced_frac=0.2, twins=8)
+    else:
+        w = wl.make_workload("mixed", [3, 0, 7], [24, 5, 30], [5, 1, 3, 8], [3, 3], seed=9, two_row_frac=0.3)
+    plan = M.Plan.from_workload(w)
+    fam = plan.families()
+    # every source term is a member exactly once
+    assert sorted(fam["term"].tolist()) == list(range(plan.n_src))
+    got = _walk(M, w, plan)
+    ii, jj = np.meshgrid(np.arange(plan.n_src), np.arange(plan.n_snk), indexing="ij")
+    ref = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii.ravel(), jj.ravel()).prod(axis=1)
+    ref = ref.reshape(plan.n_src, plan.n_snk)
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(got - ref)) <= 1e-11 * scale
+    plan.close()
+
+
+def test_generated_families_are_found(M):
+    w = wl.helium4(scale=8 / 256)
+    plan = M.Plan.from_workload(w)
+    st = plan.stats()
+    assert st["dominators"] == 8 and st["families"] == 8
+    fam = plan.families()
+    for W in range(8):
+        members = fam["term"][fam["offset"][W]:fam["offset"][W + 1]]
+        assert len(set(w.meta["src"]["family_of"][members])) == 1 and len(members) == 16
+    assert np.all(fam["rank"] == 1)
+    plan.close()
+
+
+def test_rank2_families(M):
+    w = wl.large_nucleus(scale=6 / 1024)
+    plan = M.Plan.from_workload(w)
+    st = plan.stats()
+    fam = plan.families()
+    two_rows = sum(1 for fr in w.meta["src"]["rows"] for rr in fr if len(rr) == 2)
+    assert st["rank2_family_flavours"] == two_rows
+    assert st["families"] == 6
+    plan.close()
+
+
+def test_plan_is_deterministic(M):
+    w = wl.make_workload("det", [4, 3], [20, 16], [6, 5, 4, 7], [3, 3], seed=21, two_row_frac=0.2)
+    a = M.Plan.from_workload(w).families()
+    b = M.Plan.from_workload(w).families()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def _graph(labels, n_f, dmax=1):
+    N = labels.shape[0]
+    off = np.cumsum([0] + list(n_f))
+    adj = [set() for _ in range(N)]
+    for i in range(N):
+        for j in range(i + 1, N):
+            ok = True
+            for f, n in enumerate(n_f):
+                a = list(labels[i, off[f]:off[f] + n])
+                b = list(labels[j, off[f]:off[f] + n])
+                common = 0
+                for x in set(a):
+                    common += min(a.count(x), b.count(x))
+                ok &= (n - common) <= dmax
+            if ok:
+                adj[i].add(j)
+                adj[j].add(i)
+    return adj
+
+
+def _greedy(adj):
+    """Sec. 3: pick the highest-degree remaining vertex (lowest index on ties), remove it
+    and its remaining neighbours, repeat."""
+    alive = set(range(len(adj)))
+    doms = []
+    while alive:
+        v = min(alive, key=lambda x: (-len(adj[x] & alive), x))
+        doms.append(v)
+        alive -= adj[v] | {v}
+    return doms
+
+
+def _min_dominating(adj):
+    N = len(adj)
+    for k in range(1, N + 1):
+        for S in itertools.combinations(range(N), k):
+            cov = set(S)
+            for v in S:
+                cov |= adj[v]
+            if len(cov) == N:
+                return k
+    return N
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_dominating_set(M, seed):
+    rng = np.random.default_rng(100 + seed)
+    n_f, L_f = [2, 2], [5, 5]
+    N = 11
+    labels = np.concatenate([np.sort(rng.choice(L, size=n, replace=False, shuffle=False))[None, :].repeat(1, 0)
+                             for n, L in zip(n_f, L_f)], axis=1)
+    labels = np.stack([np.concatenate([rng.choice(L, size=n, replace=False) for n, L in zip(n_f, L_f)])
+                       for _ in range(N)]).astype(np.int32)
+    plan = M.Plan(n_f, L_f, labels, np.ones(N), labels[:2], np.ones(2))
+    st = plan.stats()
+    adj = _graph(labels, n_f)
+    doms = _greedy(adj)
+    assert st["dominators"] == len(doms)
+    assert st["graph_edges"] == sum(len(a) for a in adj) // 2
+    opt = _min_dominating(adj)
+    assert opt <= len(doms)
+    # families are dominator + neighbours: every member differs from its reference in at
+    # most one label per flavour
+    fam = plan.families()
+    for W in range(len(fam["offset"]) - 1):
+        ref = fam["ref"][W]
+        for m in range(fam["offset"][W], fam["offset"][W + 1]):
+            i = fam["term"][m]
+            assert i == ref_term(labels, ref) or i in adj[ref_term(labels, ref)]
+    plan.close()
+
+
+def ref_term(labels, ref):
+    idx = np.where((labels == ref).all(axis=1))[0]
+    return int(idx[0])
+
+
+@pytest.mark.parametrize("case", ["label", "n_f", "empty", "tau"])
+def test_validation(M, case):
+    n_f, L_f = [2], [4]
+    labels = np.array([[0, 1], [2, 3]], np.int32)
+    w = np.ones(2)
+    opts = None
+    if case == "label":
+        labels = np.array([[0, 4], [2, 3]], np.int32)
+    elif case == "n_f":
+        n_f = [33]
+        labels = np.zeros((2, 33), np.int32)
+        L_f = [40]
+    elif case == "tau":
+        opts = M.default_opts()
+        opts.tau_child = 2.0
+    if case == "empty":
+        with pytest.raises(M.MHCError) as e:
+            M.mhc_plan(n_f, L_f, labels[:0], w[:0], labels, w)
+    else:
+        with pytest.raises(M.MHCError) as e:
+            M.mhc_plan(n_f, L_f, labels, w, labels, w, opts)
+    assert e.value.status == M.MHC_EINVAL
+
+
+def test_flop_count_below_fresh_lu(M):
+    w = wl.helium4(scale=4 / 256)
+    plan = M.Plan.from_workload(w)
+    st = plan.stats()
+    per_pair = st["flops_per_call"] / (plan.n_src * plan.n_snk)
+    assert 0 < per_pair < st["fresh_lu_flops_per_pair"] / 4
