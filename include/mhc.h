@@ -185,6 +185,32 @@ mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
                                    double* dw_src_dev, double* dw_snk_dev, mhc_stream_t stream);
 
 /*
+ * Allocation-free forward correlator.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let the library allocate device memory during a call,
+ * for example a process whose device memory is entirely reserved up front by its own
+ * pool allocator (where a cudaMalloc can fail or fragment the pool), or a latency-critical
+ * loop that must not pay for an allocation (cudaMalloc and cudaFree may synchronise the
+ * device).  Same arguments and result as mhc_correlator; the call allocates nothing.
+ *   - Its scratch (one partial sum per work item) is a fixed array of
+ *     MHC_NOALLOC_MAX_ITEMS entries (1 MiB) in the library's own device memory; every GPU
+ *     that loads the library holds it until the process exits.  A plan with more work
+ *     items (families x ceil(n_snk / sink tile)) is rejected with MHC_EINVAL.
+ *   - The plan's device tables must already be on the current device: call
+ *     mhc_correlator once with the plan first (that call allocates and uploads them).
+ *     Otherwise MHC_EINVAL.
+ *   - The first call on a device looks up the array's device address (a one-time set-up);
+ *     make that first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents (each work item
+ *     overwrites its own slot before it is read, so nothing needs clearing).  Calls that
+ *     overlap on the GPU race on it: issue them on one stream or otherwise in order.
+ *   - Status and refactor counters go to the plan's status word (mhc_get_status).
+ */
+#define MHC_NOALLOC_MAX_ITEMS 65536
+mhc_status mhc_correlator_noalloc(mhc_plan_t plan, const double* const* S_f,
+                                  const double* w_src_dev, const double* w_snk_dev,
+                                  double* out_dev, mhc_stream_t stream);
+
+/*
  * Per-pair determinants through the same update path (families, lemma, guards):
  *   i_dev, j_dev : device int64 [n_pairs] source and sink term indices
  *   dets_dev     : device float64 [n_pairs][F][2], det of each flavour block in the

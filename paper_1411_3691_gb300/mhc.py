@@ -26,7 +26,8 @@ MHC_NMAX = 32
 MHC_FMAX = 8
 
 EXPORTED = ["mhc_last_error", "mhc_plan_opts_default", "mhc_plan", "mhc_plan_destroy",
-            "mhc_plan_stats", "mhc_plan_families", "mhc_correlator", "mhc_correlator_backward",
+            "mhc_plan_stats", "mhc_plan_families", "mhc_correlator", "mhc_correlator_noalloc",
+            "mhc_correlator_backward",
             "mhc_pair_dets", "mhc_get_status", "mhc_batch_create", "mhc_batch_destroy",
             "mhc_batch_correlator", "mhc_batch_info", "mhc_fp64_peak"]
 
@@ -80,6 +81,7 @@ def lib():
         L.mhc_plan_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.mhc_plan_families.argtypes = [_vp, _i64p, _i64p, _i32p, _i32p, _i32p, _i64p, _i32p, _i32p]
         L.mhc_correlator.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp]
+        L.mhc_correlator_noalloc.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp]
         L.mhc_correlator_backward.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _vp, _vp,
                                               ctypes.POINTER(_vp), _vp, _vp, _vp]
         L.mhc_pair_dets.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
@@ -192,6 +194,16 @@ def mhc_correlator(plan, S, w_src=None, w_snk=None, out=None, stream=None):
     if out is None:
         out = torch.empty(2, dtype=torch.float64, device=S[0].device)
     _check(lib().mhc_correlator(_vp(plan), _S_ptrs(S), _ptr(w_src), _ptr(w_snk), _ptr(out), _stream(stream)))
+    return out
+
+
+def mhc_correlator_noalloc(plan, S, out, w_src=None, w_snk=None, stream=None):
+    """Forward correlator that allocates nothing during the call (for callers whose device
+    memory is reserved by their own allocator, or who cannot afford an allocation in the
+    loop).  `out` must be given (float64 CUDA tensor [2]).  The plan must have been used
+    once by mhc_correlator on this device; see include/mhc.h for the scratch limits."""
+    _check(lib().mhc_correlator_noalloc(_vp(plan), _S_ptrs(S), _ptr(w_src), _ptr(w_snk), _ptr(out),
+                                        _stream(stream)))
     return out
 
 
