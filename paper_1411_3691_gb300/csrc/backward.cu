@@ -1,0 +1,232 @@
+// backward.cu -- host side of the adjoint: workspace, launch, and the fixed-order final
+// reductions of the per-warp accumulators into dS_f, dw_src and dw_snk.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "bwd_impl.cuh"
+#include "plan.h"
+
+namespace mhc {
+
+cudaError_t launch_bwd_nc8(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s);
+cudaError_t launch_bwd_nc18(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s);
+cudaError_t launch_bwd_nc32(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s);
+int plan_ncmax(const Plan& p);
+mhc_status ensure_device(Plan& p);
+mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
+                         const double* w_snk, FwdArgs& a);
+
+namespace {
+
+// dS_f[a][b] = g conj(sum over (W, slot) rows labelled a, chunks, warps of the partials)
+__global__ void fin_dS_kernel(int f, int L, const int32_t* __restrict__ list_off,
+                              const int2* __restrict__ list, const double2* __restrict__ part,
+                              int n_chunks, int warps, int F, int slots_max, int Lmax,
+                              const double* __restrict__ g, double2* __restrict__ dS) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * L) return;
+  const int a = (int)(e / L), b = (int)(e % L);
+  double2 s = make_double2(0.0, 0.0);
+  for (int k = list_off[a]; k < list_off[a + 1]; k++) {
+    const int2 ws = list[k];
+    for (int c = 0; c < n_chunks; c++)
+      for (int w = 0; w < warps; w++) {
+        const int64_t cta = (int64_t)ws.x * n_chunks + c;
+        const double2 v = part[(((cta * warps + w) * F + f) * slots_max + ws.y) * Lmax + b];
+        s.x += v.x;
+        s.y += v.y;
+      }
+  }
+  const double gr = g[0], gi = g[1];
+  dS[e] = make_double2(gr * s.x + gi * s.y, gi * s.x - gr * s.y);
+}
+
+// dw_src[i] = Re(conj(g) sum_chunks part[member(i)][chunk])
+__global__ void fin_dwsrc_kernel(int64_t n_src, const int32_t* __restrict__ src_member,
+                                 const double2* __restrict__ part, int n_chunks,
+                                 const double* __restrict__ g, double* __restrict__ dw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_src) return;
+  const int64_t m = src_member[i];
+  double2 s = make_double2(0.0, 0.0);
+  for (int c = 0; c < n_chunks; c++) {
+    s.x += part[m * n_chunks + c].x;
+    s.y += part[m * n_chunks + c].y;
+  }
+  dw[i] = g[0] * s.x + g[1] * s.y;
+}
+
+// dw_snk[j] = Re(conj(g) sum_W part[W][j])
+__global__ void fin_dwsnk_kernel(int64_t n_snk, int64_t n_fam, const double2* __restrict__ part,
+                                 const double* __restrict__ g, double* __restrict__ dw) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_snk) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int64_t W = 0; W < n_fam; W++) {
+    s.x += part[W * n_snk + j].x;
+    s.y += part[W * n_snk + j].y;
+  }
+  dw[j] = g[0] * s.x + g[1] * s.y;
+}
+
+template <typename T>
+mhc_status dev_alloc(T** p, size_t count, size_t* have) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (*p && *have >= bytes) return MHC_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    set_error(std::string("mhc_correlator_backward: cudaMalloc: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MHC_ENOMEM : MHC_ECUDA;
+  }
+  *have = bytes;
+  return MHC_OK;
+}
+
+}  // namespace
+}  // namespace mhc
+
+using namespace mhc;
+
+extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
+                                              const double* w_src_dev, const double* w_snk_dev,
+                                              const double* g_out_dev, double* const* dS_f,
+                                              double* dw_src_dev, double* dw_snk_dev,
+                                              mhc_stream_t stream) {
+  if (!plan || !g_out_dev) {
+    set_error("mhc_correlator_backward: NULL plan or g_out");
+    return MHC_EINVAL;
+  }
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  for (int64_t W = 0; W < p.n_fam; W++)
+    for (int f = 0; f < p.F; f++)
+      if (p.fam_rank[W * p.F + f] == 2) {
+        set_error("mhc_correlator_backward: the adjoint of rank-2 families is not built; "
+                  "plan with opts.rank2 = 0");
+        return MHC_EUNSUPPORTED;
+      }
+  mhc_status st = ensure_device(p);
+  if (st != MHC_OK) return st;
+  BwdArgs b;
+  if ((st = fill_fwd_args(p, S_f, w_src_dev, w_snk_dev, b.a)) != MHC_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int F = p.F;
+  int ysl = 0, mn_max = 1, Mmax = 0, Lmax = 1;
+  for (int f = 0; f < F; f++) {
+    ysl += p.n_f[f];
+    mn_max = std::max(mn_max, std::max(p.n_f[f] - 1, 0) * p.n_f[f]);
+    Mmax = std::max(Mmax, p.n_f[f] - 1);
+    Lmax = std::max(Lmax, (int)p.L_f[f]);
+  }
+  ysl = std::max(ysl, 1);
+  const int kmax = std::max(p.max_members, 1);
+  int T = 64;
+  auto smem_of = [&](int t) {
+    return ((size_t)(ysl + kmax * F + kmax) * t + (size_t)t * mn_max) * sizeof(double2);
+  };
+  if (smem_of(T) > 110 * 1024) T = 32;
+  if (smem_of(T) > 220 * 1024) {
+    set_error("mhc_correlator_backward: a family is too large for the adjoint's shared memory; "
+              "plan with a smaller opts.max_family");
+    return MHC_EUNSUPPORTED;
+  }
+  const size_t smem = smem_of(T);
+  const int warps = T / 32;
+  const int n_tiles = (int)((p.n_snk + T - 1) / T);
+  const int slots_max = Mmax + kmax;
+  const size_t per_cta = (size_t)warps * F * slots_max * Lmax * sizeof(double2);
+  int n_chunks = (int)std::min<int64_t>(n_tiles, std::max<int64_t>(1, (16 * 152 + p.n_fam - 1) / p.n_fam));
+  while (n_chunks > 1 && (double)per_cta * p.n_fam * n_chunks > 1.0e9) n_chunks = (n_chunks + 1) / 2;
+  const int tiles_per_cta = (n_tiles + n_chunks - 1) / n_chunks;
+  n_chunks = (n_tiles + tiles_per_cta - 1) / tiles_per_cta;
+  const int64_t ctas = p.n_fam * n_chunks;
+
+  DevicePlan& d = p.dev;
+  if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_rows), (size_t)ctas * per_cta / sizeof(double2),
+                      &d.bwd_rows_bytes)) != MHC_OK)
+    return st;
+  if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_wsrc), (size_t)p.n_src * n_chunks,
+                      &d.bwd_wsrc_bytes)) != MHC_OK)
+    return st;
+  if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_wsnk), (size_t)p.n_fam * p.n_snk,
+                      &d.bwd_wsnk_bytes)) != MHC_OK)
+    return st;
+  // row-label index of the accumulators, per flavour: label -> (family, slot) pairs
+  if (d.bwd_index.empty()) {
+    d.bwd_index.resize(F);
+    for (int f = 0; f < F; f++) {
+      const int L = p.L_f[f], n = p.n_f[f];
+      std::vector<std::vector<std::pair<int, int>>> lists(L);
+      if (n > 0) {
+        for (int64_t W = 0; W < p.n_fam; W++) {
+          for (int m = 0; m < n - 1; m++) lists[p.fam_arow[W * p.Tn + p.off_f[f] + m]].push_back({(int)W, m});
+          for (int64_t c = 0; c < p.fam_off[W + 1] - p.fam_off[W]; c++) {
+            const int64_t mm = p.fam_off[W] + c;
+            lists[p.mem_lab[(mm * F + f) * 2]].push_back({(int)W, (int)(n - 1 + c)});
+          }
+        }
+      }
+      std::vector<int32_t> off(L + 1, 0);
+      std::vector<int2> ent;
+      for (int a = 0; a < L; a++) {
+        for (auto& x : lists[a]) ent.push_back(make_int2(x.first, x.second));
+        off[a + 1] = (int32_t)ent.size();
+      }
+      DevicePlan::BwdIndex& bi = d.bwd_index[f];
+      if (cudaMalloc(&bi.off, off.size() * sizeof(int32_t)) != cudaSuccess ||
+          cudaMalloc(&bi.ent, std::max<size_t>(ent.size(), 1) * sizeof(int2)) != cudaSuccess) {
+        set_error("mhc_correlator_backward: cudaMalloc failed for the row index");
+        return MHC_ENOMEM;
+      }
+      cudaMemcpy(bi.off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (!ent.empty()) cudaMemcpy(bi.ent, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    }
+  }
+
+  b.tiles_per_cta = tiles_per_cta;
+  b.n_chunks = n_chunks;
+  b.warps = warps;
+  b.kmax = kmax;
+  b.slots_max = slots_max;
+  b.Lmax = Lmax;
+  b.mn_max = mn_max;
+  b.ysl = ysl;
+  b.a.n_tiles = n_tiles;
+  for (int f = 0, o = 0; f < F; f++) {
+    b.a.yoff[f] = o;
+    o += p.n_f[f];
+  }
+  b.dS_part = reinterpret_cast<double2*>(d.bwd_rows);
+  b.dwsrc_part = reinterpret_cast<double2*>(d.bwd_wsrc);
+  b.dwsnk_part = reinterpret_cast<double2*>(d.bwd_wsnk);
+  const int nc = plan_ncmax(p);
+  cudaError_t e = nc <= 8 ? launch_bwd_nc8(b, T, ctas, smem, s)
+                          : (nc <= 18 ? launch_bwd_nc18(b, T, ctas, smem, s) : launch_bwd_nc32(b, T, ctas, smem, s));
+  if (e != cudaSuccess) {
+    set_error(std::string("mhc_correlator_backward: launch: ") + cudaGetErrorString(e));
+    return MHC_ECUDA;
+  }
+  for (int f = 0; f < F; f++) {
+    if (!dS_f || !dS_f[f]) continue;
+    const int L = p.L_f[f];
+    const int64_t cnt = (int64_t)L * L;
+    fin_dS_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+        f, L, d.bwd_index[f].off, d.bwd_index[f].ent, b.dS_part, n_chunks, warps, F, slots_max,
+        Lmax, g_out_dev, reinterpret_cast<double2*>(dS_f[f]));
+  }
+  if (dw_src_dev)
+    fin_dwsrc_kernel<<<(unsigned)((p.n_src + 255) / 256), 256, 0, s>>>(p.n_src, d.src_member, b.dwsrc_part,
+                                                                        n_chunks, g_out_dev, dw_src_dev);
+  if (dw_snk_dev)
+    fin_dwsnk_kernel<<<(unsigned)((p.n_snk + 255) / 256), 256, 0, s>>>(p.n_snk, p.n_fam, b.dwsnk_part,
+                                                                        g_out_dev, dw_snk_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("mhc_correlator_backward: ") + cudaGetErrorString(e));
+    return MHC_ECUDA;
+  }
+  return MHC_OK;
+}

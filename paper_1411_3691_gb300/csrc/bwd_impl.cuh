@@ -1,0 +1,388 @@
+// bwd_impl.cuh -- adjoint of the correlator (templates; instantiated per n class by
+// bwd_nc8.cu, bwd_nc18.cu, bwd_nc32.cu).
+//
+// Jacobi's formula: d det G / d G[m][q] = cof(G)[m][q].  For a work family whose members
+// share the rows A of flavour f and differ in the last row g_c, G_c = [A; g_c]:
+//   * the cofactors of the last row are y = det(A1) z for every member (they do not
+//     depend on g_c), the same cached solve as the forward pass;
+//   * the cofactors of the rows of A are linear in g_c, so the whole family contributes
+//     cof_A([A; h]) with h = sum_c gamma_c g_c, gamma_c = w_c w_j sign_c prod_{f'!=f} det_f';
+//     with A1 = the first n-1 columns of A (LU with partial pivoting, P A1 = L U1),
+//     u_m = A1^{-1} e_m, eta_m = h[0..n-1) . u_m:
+//       cof_A([A; h])[m] = det(A1) [ (h . z) (u_m ; 0) - eta_m z ]
+//     which needs no division by det G (valid for singular members).
+// The LU factors are recomputed, not stored.  When the pivot guard fires, y and
+// cof_A([A; h]) are taken from their definition (signed minors, fresh LU each).
+//
+// Scatter: each warp owns a private accumulator D[slot][label] (global memory, L1
+// resident) for its sinks; lane s owns row s (slot s < M: shared row m; slot M + c:
+// member c), so lanes never collide and every addition happens in a fixed order.  The
+// per-warp accumulators are summed in a fixed order by finalize kernels.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mhc {
+
+struct BwdArgs {
+  FwdArgs a;
+  int tiles_per_cta, n_chunks, warps, kmax, slots_max, Lmax, mn_max, ysl;
+  double2* dS_part;     // [cta][warp][F][slots_max][Lmax]
+  double2* dwsrc_part;  // [member][n_chunks]
+  double2* dwsnk_part;  // [W][n_snk]
+};
+
+namespace bwd {
+
+using dev::cd;
+
+// det of an explicit n x n matrix in local memory (LU with partial pivoting; an exactly
+// zero pivot column gives 0).  B is destroyed.
+template <int NC>
+__device__ cd det_local(cd (*B)[NC], int n) {
+  cd det = make_double2(1.0, 0.0);
+  int parity = 0;
+  for (int k = 0; k < n; k++) {
+    int p = k;
+    double best = dev::abs1(B[k][k]);
+    for (int i = k + 1; i < n; i++) {
+      const double m = dev::abs1(B[i][k]);
+      if (dev::gt_nonneg(m, best)) {
+        best = m;
+        p = i;
+      }
+    }
+    if (__double_as_longlong(best) == 0) return make_double2(0.0, 0.0);
+    if (p != k) {
+      for (int q = k; q < n; q++) {
+        const cd t = B[k][q];
+        B[k][q] = B[p][q];
+        B[p][q] = t;
+      }
+      parity ^= 1;
+    }
+    det = k == 0 ? B[k][k] : dev::cmul(det, B[k][k]);
+    const cd rc = dev::crcp(B[k][k]);
+    for (int i = k + 1; i < n; i++) {
+      const cd l = dev::cmul(B[i][k], rc);
+      for (int q = k + 1; q < n; q++) B[i][q] = dev::cfms(l, B[k][q], B[i][q]);
+    }
+  }
+  return parity ? dev::cneg(det) : det;
+}
+
+// (-1)^(r+c) det(G without row r and column c), G n x n explicit
+template <int NC>
+__device__ cd signed_minor(const cd (*G)[NC], int n, int r, int c) {
+  cd B[NC][NC];
+  int ii = 0;
+  for (int i = 0; i < n; i++) {
+    if (i == r) continue;
+    int qq = 0;
+    for (int q = 0; q < n; q++) {
+      if (q == c) continue;
+      B[ii][qq++] = G[i][q];
+    }
+    ii++;
+  }
+  const cd d = n > 1 ? det_local<NC>(B, n - 1) : make_double2(1.0, 0.0);
+  return ((r + c) & 1) ? dev::cneg(d) : d;
+}
+
+// Cofactors from their definition for a guarded block: y (cofactors of the member row,
+// written to Y with stride ys) and the rows of cof([A; h]) for the shared rows (written
+// to Mst, row-major M x n).
+template <int NC>
+__device__ void minors_block(const cd* __restrict__ S, int L, int n, const int32_t* arow,
+                             const int32_t* col, const cd* h, cd* Y, int ys, cd* Mst) {
+  const int M = n - 1;
+  cd G[NC][NC];
+  for (int i = 0; i < M; i++)
+    for (int q = 0; q < n; q++) G[i][q] = dev::ldS(S + (size_t)arow[i] * L + col[q]);
+  for (int q = 0; q < n; q++) G[M][q] = h[q];
+  for (int q = 0; q < n; q++) Y[q * ys] = signed_minor<NC>(G, n, M, q);
+  for (int m = 0; m < M; m++)
+    for (int q = 0; q < n; q++) Mst[m * n + q] = signed_minor<NC>(G, n, m, q);
+}
+
+// Shared-row factorisation kept for the adjoint: writes the rows of cof([A; h]) for the
+// shared rows (original row order) to Mst (row-major M x n).  Returns false when the
+// pivot guard fires (the caller then takes the minors).
+template <int NC, int NFIX>
+__device__ __forceinline__ bool lu_block(const cd* __restrict__ S, int L, int n_rt,
+                                         const int32_t* __restrict__ arow,
+                                         const int32_t* __restrict__ colp, const cd* h,
+                                         cd* Mst, int kp) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 1;
+  constexpr int MC = NC - 1 > 0 ? NC - 1 : 1;
+  cd A[MC][NC];
+  int perm[MC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+    const cd* row = S + (size_t)arow[i] * L;
+    perm[i] = i;
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) A[i][q] = dev::ldS(row + colp[q]);
+  }
+  int parity = 0, emin = 4096, emax = -4096;
+  bool zero = false;
+  cd rc[MC];
+  cd det = make_double2(1.0, 0.0);
+#pragma unroll UNR
+  for (int k = 0; k < M; k++) {
+    double best = dev::abs1(A[k][k]);
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const double m = dev::abs1(A[i][k]);
+      const bool sw = dev::gt_nonneg(m, best);
+      best = sw ? m : best;
+      parity ^= (int)sw;
+      const int pk = perm[k], pi = perm[i];
+      perm[k] = sw ? pi : pk;
+      perm[i] = sw ? pk : pi;
+#pragma unroll UNR
+      for (int q = 0; q < n; q++) {  // whole rows: the multipliers travel with them
+        const cd t = A[k][q];
+        A[k][q] = sw ? A[i][q] : t;
+        A[i][q] = sw ? t : A[i][q];
+      }
+    }
+    const int e = dev::expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    const cd piv = A[k][k];
+    det = (k == 0) ? piv : dev::cmul(det, piv);
+    rc[k] = dev::crcp(piv);
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const cd l = dev::cmul(A[i][k], rc[k]);
+      A[i][k] = l;
+#pragma unroll UNR
+      for (int q = k + 1; q < n; q++) A[i][q] = dev::cfms(l, A[k][q], A[i][q]);
+    }
+  }
+  if (M > 0 && (zero || emax - emin > kp)) return false;
+  const cd sd = parity ? dev::cneg(det) : det;
+  // z = [-U1^{-1} u2 ; 1]
+  cd z[NC];
+  z[M] = make_double2(1.0, 0.0);
+#pragma unroll UNR
+  for (int k = M - 1; k >= 0; k--) {
+    cd s = A[k][M];
+#pragma unroll UNR
+    for (int q = k + 1; q < M; q++) s = dev::cfma(A[k][q], z[q], s);
+    z[k] = dev::cmul(s, dev::cneg(rc[k]));
+  }
+  cd hz = dev::cmul(h[0], z[0]);
+#pragma unroll UNR
+  for (int q = 1; q < n; q++) hz = dev::cfma(h[q], z[q], hz);
+  const cd alpha = dev::cmul(sd, hz);
+  // one column of A1^{-1} per position i: u = U1^{-1} L^{-1} e_i is column perm[i]
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+    cd w[NC];
+#pragma unroll UNR
+    for (int p = 0; p < M; p++) {
+      if (p < i) {
+        w[p] = make_double2(0.0, 0.0);
+      } else if (p == i) {
+        w[p] = make_double2(1.0, 0.0);
+      } else {
+        cd s = dev::cneg(A[p][i]);
+#pragma unroll UNR
+        for (int t = i + 1; t < p; t++) s = dev::cfms(A[p][t], w[t], s);
+        w[p] = s;
+      }
+    }
+    cd u[NC];
+#pragma unroll UNR
+    for (int p = M - 1; p >= 0; p--) {
+      cd s = w[p];
+#pragma unroll UNR
+      for (int t = p + 1; t < M; t++) s = dev::cfms(A[p][t], u[t], s);
+      u[p] = dev::cmul(s, rc[p]);
+    }
+    cd eta = make_double2(0.0, 0.0);
+#pragma unroll UNR
+    for (int q = 0; q < M; q++) eta = dev::cfma(h[q], u[q], eta);
+    const cd beta = dev::cmul(sd, eta);
+    cd* row = Mst + perm[i] * n;
+#pragma unroll UNR
+    for (int q = 0; q < M; q++) row[q] = dev::cfms(beta, z[q], dev::cmul(alpha, u[q]));
+    row[M] = dev::cneg(beta);
+  }
+  return true;
+}
+
+template <int NCMAX>
+__device__ __forceinline__ bool dispatch_lu_block(int n, const cd* S, int L, const int32_t* arow,
+                                                  const int32_t* col, const cd* h, cd* Mst, int kp) {
+  switch (n) {
+    case 1: return lu_block<1, 1>(S, L, 1, arow, col, h, Mst, kp);
+    case 2: return lu_block<2, 2>(S, L, 2, arow, col, h, Mst, kp);
+    case 3: return lu_block<3, 3>(S, L, 3, arow, col, h, Mst, kp);
+    case 4: return lu_block<4, 4>(S, L, 4, arow, col, h, Mst, kp);
+    case 5: return lu_block<5, 5>(S, L, 5, arow, col, h, Mst, kp);
+    case 6: return lu_block<6, 6>(S, L, 6, arow, col, h, Mst, kp);
+    default: return lu_block<NCMAX, 0>(S, L, n, arow, col, h, Mst, kp);
+  }
+}
+
+template <int NCMAX>
+__global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
+  const FwdArgs& a = B.a;
+  extern __shared__ double2 smem[];
+  const int T = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cta = blockIdx.x;
+  const int W = cta / B.n_chunks, chunk = cta % B.n_chunks;
+  const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
+  // shared memory: y cache | dets [c][f] | dw_src accumulators [c] | staging [warp][lane][M n]
+  cd* Ysm = smem;
+  cd* Dets = Ysm + (size_t)B.ysl * T;
+  cd* AccS = Dets + (size_t)B.kmax * a.F * T;
+  cd* Stage = AccS + (size_t)B.kmax * T;
+  cd* myStage = Stage + (size_t)(warp * 32 + lane) * B.mn_max;
+  cd* Dw = B.dS_part + ((size_t)(cta * B.warps + warp) * a.F) * B.slots_max * B.Lmax;
+
+  for (int c = 0; c < kW; c++) AccS[c * T + tid] = make_double2(0.0, 0.0);
+  for (size_t e = lane; e < (size_t)a.F * B.slots_max * B.Lmax; e += 32) Dw[e] = make_double2(0.0, 0.0);
+  __syncwarp();
+
+  const int t0 = chunk * B.tiles_per_cta;
+  const int t1 = min(a.n_tiles, t0 + B.tiles_per_cta);
+  int32_t rows[NCMAX];
+  for (int tile = t0; tile < t1; tile++) {
+    const int64_t jraw = (int64_t)tile * T + tid;
+    const bool valid = jraw < a.n_snk;
+    const int64_t j = valid ? jraw : a.n_snk - 1;
+    const double wj = valid ? a.w_snk[j] : 0.0;
+
+    // ---- pass 1: cached solves, member dets (fresh where guarded), dw partials --------
+    unsigned pguard = 0;
+    int ey[MHC_FMAX];
+    for (int f = 0; f < a.F; f++) {
+      const int n = a.n_f[f];
+      ey[f] = 0;
+      if (n == 0) continue;
+      const bool g = dev::dispatch_shared<NCMAX>(
+          n, 1, a.S[f], a.L_f[f], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
+          a.snk_lab + j * a.Tn + a.off_f[f], Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f], a.kp);
+      pguard |= (unsigned)g << f;
+    }
+    double2 accj = make_double2(0.0, 0.0);
+    for (int c = 0; c < kW; c++) {
+      const int m = mem0 + c;
+      double2 prod = make_double2(1.0, 0.0);
+      for (int f = 0; f < a.F; f++) {
+        const int n = a.n_f[f];
+        cd d = make_double2(1.0, 0.0);
+        if (n > 0) {
+          bool fail = (pguard >> f) & 1;
+          const int32_t* col = a.snk_lab + j * a.Tn + a.off_f[f];
+          if (!fail)
+            d = dev::dispatch_member<NCMAX>(n, 1, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
+                                            col, Ysm + (size_t)a.yoff[f] * T + tid, T, ey[f], a.kc, &fail);
+          if (fail) {
+            dev::member_rows(a, W, m, f, 1, rows);
+            d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, col);
+          }
+        }
+        Dets[((size_t)c * a.F + f) * T + tid] = d;
+        prod = f == 0 ? d : dev::cmul(prod, d);
+      }
+      double wc = a.w_src[a.mem_term[m]];
+      if (__popc(a.mem_par[m]) & 1) wc = -wc;
+      accj.x = fma(wc, prod.x, accj.x);
+      accj.y = fma(wc, prod.y, accj.y);
+      cd& s = AccS[c * T + tid];
+      s.x = fma(wj, prod.x, s.x);
+      s.y = fma(wj, prod.y, s.y);
+    }
+    if (valid) B.dwsnk_part[(int64_t)W * a.n_snk + j] = accj;
+
+    // ---- pass 2 per flavour: h, shared-row cofactors, scatter -------------------------
+    for (int f = 0; f < a.F; f++) {
+      const int n = a.n_f[f];
+      if (n == 0) continue;
+      const int M = n - 1;
+      const cd* S = a.S[f];
+      const int L = a.L_f[f];
+      const int32_t* col = a.snk_lab + j * a.Tn + a.off_f[f];
+      const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+      cd h[NCMAX];
+      for (int q = 0; q < n; q++) h[q] = make_double2(0.0, 0.0);
+      for (int c = 0; c < kW; c++) {
+        const int m = mem0 + c;
+        double wc = a.w_src[a.mem_term[m]] * wj;
+        if (__popc(a.mem_par[m]) & 1) wc = -wc;
+        cd g = make_double2(wc, 0.0);
+        for (int f2 = 0; f2 < a.F; f2++)
+          if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + tid]);
+        const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
+        for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
+      }
+      const bool ok = ((pguard >> f) & 1) ? false
+                                          : dispatch_lu_block<NCMAX>(n, S, L, arow, col, h, myStage, a.kp);
+      if (!ok) minors_block<NCMAX>(S, L, n, arow, col, h, Ysm + (size_t)a.yoff[f] * T + tid, T, myStage);
+      __syncwarp();
+
+      // warp scatter: lane s owns accumulator row s (s < M: shared row; else member s - M)
+      cd* Df = Dw + (size_t)f * B.slots_max * B.Lmax;
+      const int nslots = M + kW;
+      for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
+        const bool act = s < nslots;
+        const int c = act && s >= M ? s - M : 0;
+        const int m = mem0 + c;
+        double wc = a.w_src[a.mem_term[m]];
+        if (__popc(a.mem_par[m]) & 1) wc = -wc;
+        cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
+        for (int jl = 0; jl < 32; jl++) {
+          const int64_t jj = (int64_t)tile * T + warp * 32 + jl;
+          if (jj >= a.n_snk) break;
+          const int ts = warp * 32 + jl;
+          cd g = make_double2(1.0, 0.0);
+          if (s >= M) {
+            g = make_double2(wc * a.w_snk[jj], 0.0);
+            for (int f2 = 0; f2 < a.F; f2++)
+              if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + ts]);
+          }
+          const int32_t* cj = a.snk_lab + jj * a.Tn + a.off_f[f];
+          const cd* st = Stage + (size_t)ts * B.mn_max + (s < M ? s * n : 0);
+          for (int q = 0; q < n; q++) {
+            const cd v = s < M ? st[q] : Ysm[(size_t)(a.yoff[f] + q) * T + ts];
+            if (act) Drow[cj[q]] = dev::cfma(g, v, Drow[cj[q]]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // dw_src partials of this chunk: fixed-order sum over the block's threads
+  for (int c = tid; c < kW; c += T) {
+    cd s = AccS[c * T];
+    for (int t = 1; t < T; t++) {
+      s.x += AccS[c * T + t].x;
+      s.y += AccS[c * T + t].y;
+    }
+    if (__popc(a.mem_par[mem0 + c]) & 1) s = dev::cneg(s);  // member sign
+    B.dwsrc_part[(int64_t)(mem0 + c) * B.n_chunks + chunk] = s;
+  }
+}
+
+}  // namespace bwd
+
+template <int NCMAX>
+cudaError_t launch_bwd_nc(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(bwd::bwd_kernel<NCMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  bwd::bwd_kernel<NCMAX><<<(unsigned)ctas, T, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace mhc

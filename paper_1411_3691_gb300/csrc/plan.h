@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/mhc.h"
 
 namespace mhc {
@@ -44,6 +46,11 @@ struct DevicePlan {
   size_t bwd_wsrc_bytes = 0;
   double* bwd_wsnk = nullptr;    // [n_snk][2] per family-chunk partials
   size_t bwd_wsnk_bytes = 0;
+  struct BwdIndex {
+    int32_t* off = nullptr;      // [L_f + 1]
+    int2* ent = nullptr;         // (family, slot) of every accumulator row of label a
+  };
+  std::vector<BwdIndex> bwd_index;  // per flavour
 };
 
 struct Plan {

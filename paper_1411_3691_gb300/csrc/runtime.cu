@@ -45,6 +45,10 @@ void free_device(DevicePlan& d) {
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& bi : d.bwd_index) {
+    if (bi.off) cudaFree(bi.off);
+    if (bi.ent) cudaFree(bi.ent);
+  }
   d = DevicePlan();
 }
 

@@ -4,11 +4,6 @@
 using namespace mhc;
 
 extern "C" {
-mhc_status mhc_correlator_backward(mhc_plan_t, const double* const*, const double*, const double*,
-                                   const double*, double* const*, double*, double*, mhc_stream_t) {
-  set_error("mhc_correlator_backward: not built yet");
-  return MHC_EUNSUPPORTED;
-}
 mhc_status mhc_batch_create(mhc_batch_t* out, int32_t, const mhc_plan_t*) {
   if (out) *out = nullptr;
   set_error("mhc_batch_create: not built yet");
