@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="mhc", choices=["mhc", "reference"])
     ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-sequential comparison")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward comparison")
     return ap.parse_args()
 
 
@@ -263,6 +265,12 @@ def run_gpu(args):
         e2e_ms = float(t.item())
     h2d = sum(h.numel() * h.element_size() for h in hS)
 
+    adjoint = None if args.no_adjoint else time_adjoint(mhc, plan, S, flush, stream, ms_per_step, pairs)
+    batched = None if (args.no_batch or rank != 0) else time_batch(mhc, flush, stream)
+
+    if batched:
+        batched["frac_of_fp64_peak"] = batched["tflops"] / (peak_flops / 1e12)
+
     line = None
     if rank == 0:
         line = {
@@ -283,6 +291,8 @@ def run_gpu(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "refactors_per_step": refactor_pairs,
+            "adjoint": adjoint,
+            "batched": batched,
             "C": [float(out[0].item()), float(out[1].item())],
         }
         if not args.no_cpu_baseline:
@@ -292,6 +302,78 @@ def run_gpu(args):
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def time_adjoint(mhc, plan, S, flush, stream, fwd_ms, pairs, steps=5):
+    """Backward (dS_f, dw_src, dw_snk for L = Re C) of the same workload, CUDA events."""
+    import torch
+    g = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
+    dS = [torch.empty_like(s) for s in S]
+    dws = torch.empty(plan.n_src, dtype=torch.float64, device="cuda")
+    dwk = torch.empty(plan.n_snk, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        mhc.mhc_correlator_backward(plan.handle, S, g, None, None, dS, dws, dwk)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mhc.mhc_correlator_backward(plan.handle, S, g, None, None, dS, dws, dwk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    plan.status()
+    return {"ms_per_step": ms, "ratio_vs_forward": ms / fwd_ms, "pairs_per_s": pairs / (ms * 1e-3),
+            "outputs": "dS_f (2 x 48 x 48 complex), dw_src [4096], dw_snk [4096]; L = Re C",
+            "gpu_launches_per_step": 5}
+
+
+def time_batch(mhc, flush, stream, count=64, reps=3):
+    """64 independent correlators of mixed n_f in one persistent launch under a CUDA graph,
+    against 64 sequential mhc_correlator calls on the same plans and propagators."""
+    import torch
+    from paper_1411_3691_gb300 import workloads as wl
+    items = wl.batch(count)
+    plans = [mhc.Plan.from_workload(w) for w in items]
+    S = [[torch.from_numpy(s).cuda() for s in w.S] for w in items]
+    pairs = sum(w.pairs for w in items)
+    batch = mhc.mhc_batch_create([p.handle for p in plans])
+    T, n_items = mhc.mhc_batch_info(batch)
+    outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in items]
+    mhc.mhc_batch_correlator(batch, S, outs)
+    for p, Sk, o in zip(plans, S, outs):
+        p.correlator(Sk, out=o)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        tot = 0.0
+        for r in range(reps):
+            flush.fill_(float(r))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    batch_ms = timed(lambda: mhc.mhc_batch_correlator(batch, S, outs))
+    seq_ms = timed(lambda: [p.correlator(Sk, out=o) for p, Sk, o in zip(plans, S, outs)])
+    flops = sum(p.stats()["flops_per_call"] for p in plans)
+    for p in plans:
+        p.status()
+    mhc.mhc_batch_destroy(batch)
+    for p in plans:
+        p.close()
+    return {"workload": f"{count} correlators: n_f ~ U{{3,6,9,12,18}} per flavour, L = 12 ceil(n/3) + 12, "
+                        "terms per side log-U[256, 16384], family sizes U[1, 32] (seeds 2000 + b)",
+            "pairs": pairs, "ms": batch_ms, "pairs_per_s": pairs / (batch_ms * 1e-3),
+            "tflops": flops / (batch_ms * 1e-3) / 1e12,
+            "sequential_ms": seq_ms, "sequential_pairs_per_s": pairs / (seq_ms * 1e-3),
+            "speedup_vs_sequential": seq_ms / batch_ms, "tile": T, "work_items": n_items,
+            "graph": True}
 
 
 def main():

@@ -69,10 +69,15 @@ typedef struct {
   double tau_child;    /* refactor one member when |det| < tau_child * |row| * |y|,
                           the normalised lemma factor (powers of two).          1e-3  */
   int32_t sink_tile;   /* sinks per thread block; 0 = chosen by n class.        0     */
-  int32_t rank2;       /* 1: families may differ in two rows per flavour (rank-2
-                          update by a 2x2 generalised cofactor); 0: one row.    1     */
+  int32_t rank2;       /* 1: families may differ in two rows per flavour with
+                          n_f >= 10 (rank-2 update by a 2x2 generalised cofactor);
+                          0: one row.                                           1     */
   int32_t max_family;  /* largest number of members per family, 1..64.          32    */
-  int32_t reserved[8];
+  int32_t one_sided;   /* 1: only source-side families (Sec. 3 as printed); 0: sink
+                          terms are grouped too, and each (source family, sink
+                          family) block shares adj(B) of its common rows and
+                          columns (two-sided update).                           0     */
+  int32_t reserved[7];
 } mhc_plan_opts;
 
 /* Planner and run statistics. */
@@ -93,7 +98,9 @@ typedef struct {
   /* device counters of the last mhc_correlator / backward call (mhc_get_status): */
   int64_t refactor_parent;       /* (member, sink, flavour) refactored by the pivot guard */
   int64_t refactor_child;        /* (member, sink, flavour) refactored by the lemma guard */
-  int64_t reserved[6];
+  int64_t sink_families;         /* sink-side families (two-sided update)             */
+  int64_t two_sided_blocks;      /* (family, sink family, flavour) blocks sharing adj(B) */
+  int64_t reserved[4];
 } mhc_stats;
 
 /* Thread-local message describing the last failure of this thread's last call. */
@@ -153,6 +160,24 @@ mhc_status mhc_plan_stats(mhc_plan_t plan, mhc_stats* out);
 mhc_status mhc_plan_families(mhc_plan_t plan, int64_t* n_families, int64_t* fam_member_offset,
                              int32_t* fam_rank, int32_t* fam_rows, int32_t* fam_ref,
                              int64_t* member_term, int32_t* member_sign, int32_t* member_labels);
+
+/*
+ * Export the sink-side families of the two-sided update (host; for inspection and
+ * tests).  Sinks are evaluated in family-major order; for every flavour the columns of a
+ * sink are aligned to its family's reference tuple with the family's changed column last,
+ * so all members of a family share their first n_f - 1 columns.  NULL arrays skip.
+ *   n_sink_families : number of sink families Q
+ *   order           : int32 [n_snk]; original sink index at each position
+ *   labels          : int32 [n_snk][sum n_f]; aligned column labels at each position
+ *   parity          : int32 [n_snk]; bit f = parity of the column permutation (the
+ *                     determinant in the original column order is (-1)^bit times the
+ *                     determinant in the aligned order)
+ *   family          : int32 [n_snk]; sink family of each position
+ *   two_sided       : int32 [Q]; 1 when the family shares adj(B) (two or more sinks)
+ * With opts->one_sided every sink is its own family and the update is one-sided.
+ */
+mhc_status mhc_plan_sinks(mhc_plan_t plan, int64_t* n_sink_families, int32_t* order,
+                          int32_t* labels, int32_t* parity, int32_t* family, int32_t* two_sided);
 
 /*
  * Forward correlator on the GPU.

@@ -19,7 +19,7 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libmhc.so")
 
 SOURCES = ["planner.cpp", "runtime.cu", "forward.cu", "fwd_nc8.cu", "fwd_nc18.cu", "fwd_nc32.cu",
-           "backward.cu", "bwd_nc8.cu", "bwd_nc18.cu", "bwd_nc32.cu", "batch.cu", "probe.cu", "stubs.cu", "noalloc.cu"]
+           "backward.cu", "bwd_nc8.cu", "bwd_nc18.cu", "bwd_nc32.cu", "batch.cu", "probe.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1,0 +1,394 @@
+// batch.cu -- many independent correlators in one persistent launch, captured once into
+// a CUDA graph, with the sink tile (threads per block) chosen by measurement.
+//
+// The work items of all correlators, (correlator, family, sink tile), are listed on the
+// host in decreasing order of their FLOP count (largest first), and a grid of one wave of
+// thread blocks pulls them from that list through one atomic counter.  Each item writes
+// its partial sum to a slot indexed by the item, not by the block that ran it, and each
+// correlator's slots are summed in a fixed order afterwards: results do not depend on the
+// dynamic assignment.  There is no waiting between blocks, so no bounded wait is needed.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.h"
+
+struct mhc_batch_s;
+
+namespace mhc {
+
+int plan_ncmax(const Plan& p);
+mhc_status ensure_device(Plan& p);
+mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
+                         const double* w_snk, FwdArgs& a);
+void plan_slots(const Plan& p, int* yoff, int* total);
+
+namespace {
+
+// fixed-order sum of each correlator's item partials (one block per correlator)
+__global__ void __launch_bounds__(256) batch_reduce(const double2* __restrict__ partials,
+                                                    const int64_t* __restrict__ part_off,
+                                                    double* const* __restrict__ outs) {
+  __shared__ double2 red[8];
+  const int b = blockIdx.x;
+  const int64_t i0 = part_off[b], i1 = part_off[b + 1];
+  double2 s = make_double2(0.0, 0.0);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    s.x += partials[i].x;
+    s.y += partials[i].y;
+  }
+  s = dev::warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      t.x += red[w].x;
+      t.y += red[w].y;
+    }
+    outs[b][0] = t.x;
+    outs[b][1] = t.y;
+  }
+}
+
+// deterministic finite scratch propagators for the autotuner: entries in [-1, 1] + 2 I
+__global__ void scratch_S(double2* S, int L, uint32_t seed) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * L) return;
+  uint32_t x = (uint32_t)e * 2654435761u ^ seed;
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  uint32_t y = x * 0x846ca68bu;
+  y ^= y >> 16;
+  const double re = (double)(x & 0xffffff) / 8388608.0 - 1.0;
+  const double im = (double)(y & 0xffffff) / 8388608.0 - 1.0;
+  S[e] = make_double2(re + ((e / L) == (e % L) ? 2.0 : 0.0), im);
+}
+
+}  // namespace
+
+// One launch configuration of a batch (a sink tile T).
+struct BatchShape {
+  int T = 0, grid = 0, ncmax = 8;
+  size_t smem = 0;
+  int64_t n_items = 0;
+  std::vector<BatchItem> items;
+  std::vector<int64_t> part_off;  // [count + 1]
+  std::vector<int> n_tiles;       // per correlator
+};
+
+}  // namespace mhc
+
+using namespace mhc;
+
+struct mhc_batch_s {
+  int count = 0;
+  int device = -1;
+  std::vector<Plan*> plans;
+  BatchShape shape;
+  FwdArgs* d_desc = nullptr;
+  BatchItem* d_items = nullptr;
+  int64_t* d_part_off = nullptr;
+  double2* d_partials = nullptr;
+  unsigned long long* d_head = nullptr;
+  double** d_outs = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;  // S and out pointers the graph was captured with
+  std::vector<double> tune_ms;   // measured time per candidate tile (32, 64, 128)
+};
+
+namespace {
+
+BatchShape make_shape(const mhc_batch_s& b, int T) {
+  BatchShape sh;
+  sh.T = T;
+  struct Cost {
+    double c;
+    BatchItem it;
+  };
+  std::vector<Cost> all;
+  sh.part_off.push_back(0);
+  int max_slots = 1;
+  for (int k = 0; k < b.count; k++) {
+    const Plan& p = *b.plans[k];
+    const int nt = (int)((p.n_snk + T - 1) / T);
+    sh.n_tiles.push_back(nt);
+    sh.ncmax = std::max(sh.ncmax, plan_ncmax(p));
+    int yoff[MHC_FMAX], slots = 0;
+    plan_slots(p, yoff, &slots);
+    max_slots = std::max(max_slots, slots);
+    for (int64_t W = 0; W < p.n_fam; W++) {
+      double c = 0.0;
+      const double kW = (double)(p.fam_off[W + 1] - p.fam_off[W]);
+      for (int f = 0; f < p.F; f++) {
+        const int n = p.n_f[f], rho = p.fam_rank[W * p.F + f];
+        if (n > 0) c += flops_shared_rows(n, rho) + kW * flops_member(n, rho);
+      }
+      for (int t = 0; t < nt; t++) {
+        const double width = (double)std::min<int64_t>(T, p.n_snk - (int64_t)t * T);
+        all.push_back({c * width, BatchItem{k, (int32_t)W, t, 0}});
+      }
+    }
+    sh.part_off.push_back(sh.part_off.back() + p.n_fam * nt);
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Cost& x, const Cost& y) { return x.c > y.c; });
+  for (auto& c : all) sh.items.push_back(c.it);
+  sh.n_items = (int64_t)sh.items.size();
+  sh.smem = forward_smem_bytes(max_slots, T);
+  int occ = 1;
+  if (sh.ncmax <= 8)
+    occ = batch_occupancy_nc8(T, sh.smem);
+  else if (sh.ncmax <= 18)
+    occ = batch_occupancy_nc18(T, sh.smem);
+  else
+    occ = batch_occupancy_nc32(T, sh.smem);
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device);
+  sh.grid = (int)std::min<int64_t>((int64_t)sms * occ, std::max<int64_t>(sh.n_items, 1));
+  return sh;
+}
+
+mhc_status fill_descs(mhc_batch_s& b, const BatchShape& sh, const double* const* const* S,
+                      std::vector<FwdArgs>& desc) {
+  desc.resize(b.count);
+  for (int k = 0; k < b.count; k++) {
+    mhc_status st = fill_fwd_args(*b.plans[k], S[k], nullptr, nullptr, desc[k]);
+    if (st != MHC_OK) return st;
+    desc[k].snk_orig = nullptr;  // the batched launch takes the one-sided update
+    desc[k].n_tiles = sh.n_tiles[k];
+  }
+  return MHC_OK;
+}
+
+mhc_status upload_shape(mhc_batch_s& b, const BatchShape& sh) {
+  if (b.d_items) cudaFree(b.d_items);
+  if (b.d_part_off) cudaFree(b.d_part_off);
+  if (b.d_partials) cudaFree(b.d_partials);
+  b.d_items = nullptr;
+  b.d_part_off = nullptr;
+  b.d_partials = nullptr;
+  if (cudaMalloc(&b.d_items, std::max<size_t>(sh.items.size(), 1) * sizeof(BatchItem)) != cudaSuccess ||
+      cudaMalloc(&b.d_part_off, sh.part_off.size() * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&b.d_partials, std::max<int64_t>(sh.part_off.back(), 1) * sizeof(double2)) != cudaSuccess) {
+    set_error("mhc_batch: cudaMalloc failed");
+    return MHC_ENOMEM;
+  }
+  if (!sh.items.empty())
+    cudaMemcpy(b.d_items, sh.items.data(), sh.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+  cudaMemcpy(b.d_part_off, sh.part_off.data(), sh.part_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  return MHC_OK;
+}
+
+cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b.d_head, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (sh.ncmax <= 8)
+    e = launch_batch_nc8(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
+  else if (sh.ncmax <= 18)
+    e = launch_batch_nc18(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
+  else
+    e = launch_batch_nc32(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
+  if (e != cudaSuccess) return e;
+  batch_reduce<<<b.count, 256, 0, s>>>(b.d_partials, b.d_part_off, b.d_outs);
+  return cudaGetLastError();
+}
+
+void destroy(mhc_batch_s* b) {
+  if (!b) return;
+  if (b->device >= 0) {
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  void* ptrs[] = {b->d_desc, b->d_items, b->d_part_off, b->d_partials, b->d_head, b->d_outs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* plans) {
+  if (!out || count <= 0 || !plans) {
+    set_error("mhc_batch_create: bad argument");
+    return MHC_EINVAL;
+  }
+  *out = nullptr;
+  mhc_batch_s* b = new mhc_batch_s();
+  b->count = count;
+  cudaGetDevice(&b->device);
+  for (int k = 0; k < count; k++) {
+    if (!plans[k]) {
+      delete b;
+      set_error("mhc_batch_create: NULL plan");
+      return MHC_EINVAL;
+    }
+    Plan* p = reinterpret_cast<Plan*>(plans[k]);
+    mhc_status st = ensure_device(*p);
+    if (st != MHC_OK) {
+      delete b;
+      return st;
+    }
+    b->plans.push_back(p);
+  }
+  if (cudaMalloc(&b->d_desc, sizeof(FwdArgs) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_head, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&b->d_outs, sizeof(double*) * count) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    destroy(b);
+    set_error("mhc_batch_create: CUDA allocation failed");
+    return MHC_ENOMEM;
+  }
+  // ---- autotune the sink tile on scratch propagators -------------------------------
+  std::vector<std::vector<double2*>> scratch(count);
+  std::vector<std::vector<const double*>> sp(count);
+  std::vector<const double* const*> S(count);
+  double* scratch_out = nullptr;
+  cudaMalloc(&scratch_out, sizeof(double) * 2 * count);
+  std::vector<double*> outs(count);
+  for (int k = 0; k < count; k++) {
+    const Plan& p = *b->plans[k];
+    for (int f = 0; f < p.F; f++) {
+      double2* s = nullptr;
+      const int L = p.L_f[f];
+      if (cudaMalloc(&s, sizeof(double2) * L * L) != cudaSuccess) {
+        destroy(b);
+        set_error("mhc_batch_create: scratch allocation failed");
+        return MHC_ENOMEM;
+      }
+      scratch_S<<<(L * L + 255) / 256, 256, 0, b->cap>>>(s, L, 977u * k + f);
+      scratch[k].push_back(s);
+      sp[k].push_back(reinterpret_cast<const double*>(s));
+    }
+    S[k] = sp[k].data();
+    outs[k] = scratch_out + 2 * k;
+  }
+  cudaMemcpy(b->d_outs, outs.data(), sizeof(double*) * count, cudaMemcpyHostToDevice);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  const int cands[3] = {32, 64, 128};
+  mhc_status st = MHC_OK;
+  for (int T : cands) {
+    BatchShape sh = make_shape(*b, T);
+    if (sh.smem > 200 * 1024) {
+      b->tune_ms.push_back(-1.0);
+      continue;
+    }
+    std::vector<FwdArgs> desc;
+    if ((st = fill_descs(*b, sh, S.data(), desc)) != MHC_OK) break;
+    cudaMemcpy(b->d_desc, desc.data(), sizeof(FwdArgs) * count, cudaMemcpyHostToDevice);
+    if ((st = upload_shape(*b, sh)) != MHC_OK) break;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; rep++) {
+      cudaEventRecord(e0, b->cap);
+      cudaError_t e = enqueue(*b, sh, b->cap);
+      cudaEventRecord(e1, b->cap);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error(std::string("mhc_batch_create: tuning launch failed: ") + cudaGetErrorString(e));
+        st = MHC_ECUDA;
+        break;
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (st != MHC_OK) break;
+    b->tune_ms.push_back(ms);
+    if (ms < best) {
+      best = ms;
+      b->shape = std::move(sh);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto& v : scratch)
+    for (auto* s : v) cudaFree(s);
+  cudaFree(scratch_out);
+  if (st == MHC_OK && b->shape.T == 0) {
+    set_error("mhc_batch_create: no launch shape fits in shared memory");
+    st = MHC_EUNSUPPORTED;
+  }
+  if (st == MHC_OK) st = upload_shape(*b, b->shape);
+  if (st != MHC_OK) {
+    destroy(b);
+    return st;
+  }
+  *out = reinterpret_cast<mhc_batch_t>(b);
+  return MHC_OK;
+}
+
+void mhc_batch_destroy(mhc_batch_t batch) { destroy(reinterpret_cast<mhc_batch_s*>(batch)); }
+
+mhc_status mhc_batch_correlator(mhc_batch_t batch, const double* const* const* S, double* const* outs,
+                                mhc_stream_t stream) {
+  if (!batch || !S || !outs) {
+    set_error("mhc_batch_correlator: NULL argument");
+    return MHC_EINVAL;
+  }
+  mhc_batch_s& b = *reinterpret_cast<mhc_batch_s*>(batch);
+  std::vector<const void*> key;
+  for (int k = 0; k < b.count; k++) {
+    if (!S[k] || !outs[k]) {
+      set_error("mhc_batch_correlator: NULL propagator list or output");
+      return MHC_EINVAL;
+    }
+    for (int f = 0; f < b.plans[k]->F; f++) key.push_back(S[k][f]);
+    key.push_back(outs[k]);
+  }
+  if (!b.exec || key != b.key) {
+    // new pointers: refresh the descriptors and capture the launch sequence once
+    std::vector<FwdArgs> desc;
+    mhc_status st = fill_descs(b, b.shape, S, desc);
+    if (st != MHC_OK) return st;
+    if (cudaStreamSynchronize(b.cap) != cudaSuccess ||
+        cudaMemcpy(b.d_desc, desc.data(), sizeof(FwdArgs) * b.count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b.d_outs, outs, sizeof(double*) * b.count, cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("mhc_batch_correlator: descriptor upload failed");
+      return MHC_ECUDA;
+    }
+    if (b.exec) {
+      cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(b, b.shape, b.cap);
+      e = cudaStreamEndCapture(b.cap, &g);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      set_error(std::string("mhc_batch_correlator: graph capture: ") + cudaGetErrorString(e));
+      return MHC_ECUDA;
+    }
+    b.key = key;
+  }
+  cudaError_t e = cudaGraphLaunch(b.exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_error(std::string("mhc_batch_correlator: graph launch: ") + cudaGetErrorString(e));
+    return MHC_ECUDA;
+  }
+  return MHC_OK;
+}
+
+mhc_status mhc_batch_info(mhc_batch_t batch, int32_t* threads_per_block, int32_t* tiles_total) {
+  if (!batch) {
+    set_error("mhc_batch_info: NULL batch");
+    return MHC_EINVAL;
+  }
+  const mhc_batch_s& b = *reinterpret_cast<const mhc_batch_s*>(batch);
+  if (threads_per_block) *threads_per_block = b.shape.T;
+  if (tiles_total) *tiles_total = (int32_t)b.shape.n_items;
+  return MHC_OK;
+}
+
+}  // extern "C"

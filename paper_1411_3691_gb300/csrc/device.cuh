@@ -224,6 +224,40 @@ __device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_
   }
 }
 
+// Two-sided update: the sink belongs to a sink family whose members share every column but
+// the last, so G = [[B, a], [g^T, alpha]] with B the block of shared rows and shared
+// columns.  By the Schur complement det G = alpha det B - g^T adj(B) a, i.e. det G = g' . y
+// with g' the member's full row and y = [-adj(B) a ; det B].  adj(B) (row-major, then
+// det B) is shared by the whole (family, sink family) block.  Writes y like shared_rows
+// (rank 1) and the member-guard exponent scale to *ey.
+template <int NC, int NFIX>
+__device__ __forceinline__ void kapply(const cd* __restrict__ S, int L, int n_rt,
+                                       const int32_t* __restrict__ arow,
+                                       const int32_t* __restrict__ colp, const cd* __restrict__ K,
+                                       cd* __restrict__ Y, int ys, int* ey) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 1;
+  constexpr int MC = NC - 1 > 0 ? NC - 1 : 1;
+  const int cj = colp[M];
+  cd av[MC];
+#pragma unroll UNR
+  for (int t = 0; t < M; t++) av[t] = ldS(S + (size_t)arow[t] * L + cj);
+  int ez = -4096;
+#pragma unroll UNR
+  for (int u = 0; u < M; u++) {
+    cd v = cmul(__ldg(K + u * M), av[0]);
+#pragma unroll UNR
+    for (int t = 1; t < M; t++) v = cfma(__ldg(K + u * M + t), av[t], v);
+    const cd y = cneg(v);
+    Y[u * ys] = y;
+    ez = max(ez, expo(y));
+  }
+  const cd dB = __ldg(K + M * M);
+  Y[M * ys] = dB;
+  *ey = max(ez, expo(dB));
+}
+
 // Fresh determinant of one n x n block by LU with partial pivoting (the refactor path):
 // rows S[rows[m]], columns col[q].
 template <int NC, int NFIX>

@@ -37,9 +37,18 @@ size_t forward_smem_bytes(int slots, int tile) {
   return cache + queue;
 }
 
-cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t items, size_t smem,
-                           double* out, cudaStream_t s) {
-  cudaError_t e;
+cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,
+                           size_t smem, double* out, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (a.snk_orig) {  // two-sided update: adj(B) of every (family, sink family) block first
+    if (ncmax <= 8)
+      e = launch_kfac_nc8(a, n_fam, s);
+    else if (ncmax <= 18)
+      e = launch_kfac_nc18(a, n_fam, s);
+    else
+      e = launch_kfac_nc32(a, n_fam, s);
+    if (e != cudaSuccess) return e;
+  }
   if (ncmax <= 8)
     e = launch_fwd_nc8(a, tile, items, smem, s);
   else if (ncmax <= 18)

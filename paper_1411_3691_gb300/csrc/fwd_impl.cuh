@@ -23,7 +23,14 @@ struct QEntry {
   int32_t fail;    // flavours to refactor (bit f)
   int32_t pad;
   double2 prod;    // product of the flavours that did not fail
+  double w;        // signed w_i w_j of the pair
+  double pad2;
 };
+
+// column labels of the sink at position j (aligned order in the two-sided update)
+__device__ __forceinline__ const int32_t* sink_cols(const FwdArgs& a, int64_t j) {
+  return (a.snk_orig ? a.snk_pos : a.snk_lab) + j * a.Tn;
+}
 
 template <int NCMAX>
 __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
@@ -32,6 +39,7 @@ __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int
   if (lane < count) {
     const QEntry e = q[lane];
     const int64_t j = jbase + e.lane;
+    const int32_t* cols = sink_cols(a, j);
     double2 prod = e.prod;
     int32_t rows[NCMAX];
     for (int f = 0; f < a.F; f++) {
@@ -39,29 +47,27 @@ __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int
       const int n = a.n_f[f];
       const int rho = a.fam_rank[(int64_t)W * a.F + f];
       dev::member_rows(a, W, e.member, f, rho, rows);
-      const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows,
-                                                   a.snk_lab + j * a.Tn + a.off_f[f]);
+      const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, cols + a.off_f[f]);
       prod = dev::cmul(prod, d);
     }
-    const int32_t sgn = a.mem_par[e.member];
-    double w = a.w_src[a.mem_term[e.member]] * a.w_snk[j];
-    if (__popc(sgn) & 1) w = -w;
-    acc.x = fma(w, prod.x, acc.x);
-    acc.y = fma(w, prod.y, acc.y);
+    acc.x = fma(e.w, prod.x, acc.x);
+    acc.y = fma(e.w, prod.y, acc.y);
   }
 }
 
+// One work item (family W x sink tile) by the whole thread block; the block's sum goes
+// to *partial.  Shared by the per-plan launch and the persistent batched launch.
 template <int NCMAX>
-__global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
-  extern __shared__ double2 smem[];
+__device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, double2* smem,
+                                         double2* partial) {
   const int T = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t item = blockIdx.x;
-  const int W = (int)(item / a.n_tiles);
-  const int tile = (int)(item % a.n_tiles);
   const int64_t jraw = (int64_t)tile * T + tid;
   const bool valid = jraw < a.n_snk;
-  const int64_t j = valid ? jraw : a.n_snk - 1;
+  const int64_t j = valid ? jraw : a.n_snk - 1;  // sink position
+  const int32_t* cols = sink_cols(a, j);
+  const int Q = a.snk_orig ? a.snk_q[j] : -1;
+  const bool qtwo = Q >= 0 && a.q_two[Q];
   const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
   QEntry* queue = reinterpret_cast<QEntry*>(smem + (size_t)a.slots * T) + warp * kQueueCap;
   double2* Y = smem + tid;
@@ -74,14 +80,21 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
     ey[f] = 0;
     if (n == 0) continue;
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
-    const bool g = dev::dispatch_shared<NCMAX>(
-        n, rho, a.S[f], a.L_f[f], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
-        a.snk_lab + j * a.Tn + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, &ey[f], a.kp);
-    pguard |= (unsigned)g << f;
+    const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+    if (qtwo && rho == 1 && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+      dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
+                                  a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f],
+                                  Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+    } else {
+      const bool g = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
+                                                 Y + (size_t)a.yoff[f] * T, T, &ey[f], a.kp);
+      pguard |= (unsigned)g << f;
+    }
   }
 
   // ---- per member: one dot product per flavour --------------------------------------
-  const double wj = valid ? a.w_snk[j] : 0.0;
+  double wj = valid ? a.w_snk[a.snk_orig ? a.snk_orig[j] : j] : 0.0;
+  if (a.snk_orig && (__popc(a.snk_par[j]) & 1)) wj = -wj;
   double2 acc = make_double2(0.0, 0.0);
   int qn = 0;
   unsigned long long n_parent = 0, n_child = 0;
@@ -97,7 +110,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
       bool cf = false;
       const double2 d = dev::dispatch_member<NCMAX>(
           n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
-          a.snk_lab + j * a.Tn + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, ey[f], a.kc, &cf);
+          cols + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, ey[f], a.kc, &cf);
       if (cf) {
         fail |= 1u << f;
       } else {
@@ -106,9 +119,9 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
       }
     }
     const bool need = valid && fail != 0;
+    double w = a.w_src[a.mem_term[m]] * wj;
+    if (__popc(a.mem_par[m]) & 1) w = -w;
     if (!fail) {
-      double w = a.w_src[a.mem_term[m]] * wj;
-      if (__popc(a.mem_par[m]) & 1) w = -w;
       acc.x = fma(w, prod.x, acc.x);
       acc.y = fma(w, prod.y, acc.y);
     }
@@ -122,6 +135,8 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
         e.fail = (int32_t)fail;
         e.pad = 0;
         e.prod = prod;
+        e.w = w;
+        e.pad2 = 0.0;
         queue[pos] = e;
         n_parent += __popc(fail & pguard);
         n_child += __popc(fail & ~pguard);
@@ -155,13 +170,20 @@ __global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
       s.x += red[w].x;
       s.y += red[w].y;
     }
-    a.partials[item] = s;
+    *partial = s;
     if (!dev::finite2(s)) atomicOr(&a.counters[0], kStatusNonFinite);
   }
   if (lane == 0 && (n_parent | n_child)) {
     atomicAdd(&a.counters[1], n_parent);
     atomicAdd(&a.counters[2], n_child);
   }
+}
+
+template <int NCMAX>
+__global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
+  extern __shared__ double2 smem[];
+  const int64_t item = blockIdx.x;
+  fwd_item<NCMAX>(a, (int)(item / a.n_tiles), (int)(item % a.n_tiles), smem, &a.partials[item]);
 }
 
 // Per-pair determinants through the same update path (one thread per pair).
@@ -213,7 +235,148 @@ __global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pai
   if (path) path[p] = bits;
 }
 
+// adj(B) of every two-sided (family, sink family, flavour) block: one thread per block.
+// B = S[shared rows][shared columns] ((n-1) x (n-1)); LU with partial pivoting (the same
+// pivot rule and guard as shared_rows), then adj(B) = det(B) B^{-1} column by column.
+template <int NCMAX>
+__global__ void __launch_bounds__(128) kfac_kernel(const FwdArgs a, int64_t n_fam) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_fam * a.n_q * a.F) return;
+  const int f = (int)(t % a.F);
+  const int64_t wq = t / a.F;
+  const int Q = (int)(wq % a.n_q);
+  const int W = (int)(wq / a.n_q);
+  const int n = a.n_f[f];
+  if (n == 0 || !a.q_two[Q] || a.fam_rank[(int64_t)W * a.F + f] != 1) return;
+  const int M = n - 1;
+  constexpr int MC = NCMAX - 1;
+  const dev::cd* S = a.S[f];
+  const int L = a.L_f[f];
+  const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+  const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
+  dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
+  dev::cd B[MC][MC];
+  int perm[MC];
+  for (int i = 0; i < M; i++) {
+    perm[i] = i;
+    for (int u = 0; u < M; u++) B[i][u] = dev::ldS(S + (size_t)arow[i] * L + scol[u]);
+  }
+  int parity = 0, emin = 4096, emax = -4096;
+  bool zero = false;
+  dev::cd rc[MC];
+  dev::cd det = make_double2(1.0, 0.0);
+  for (int k = 0; k < M; k++) {
+    double best = dev::abs1(B[k][k]);
+    for (int i = k + 1; i < M; i++) {
+      const double m = dev::abs1(B[i][k]);
+      if (dev::gt_nonneg(m, best)) {
+        best = m;
+        parity ^= 1;
+        for (int u = 0; u < M; u++) {
+          const dev::cd x = B[k][u];
+          B[k][u] = B[i][u];
+          B[i][u] = x;
+        }
+        const int pi = perm[i];
+        perm[i] = perm[k];
+        perm[k] = pi;
+      }
+    }
+    const int e = dev::expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    det = (k == 0) ? B[k][k] : dev::cmul(det, B[k][k]);
+    rc[k] = dev::crcp(B[k][k]);
+    for (int i = k + 1; i < M; i++) {
+      const dev::cd l = dev::cmul(B[i][k], rc[k]);
+      B[i][k] = l;
+      for (int u = k + 1; u < M; u++) B[i][u] = dev::cfms(l, B[k][u], B[i][u]);
+    }
+  }
+  const bool guard = M > 0 && (zero || emax - emin > a.kp);
+  a.kguard[t] = guard ? 1 : 0;
+  if (guard) return;
+  const dev::cd sd = parity ? dev::cneg(det) : det;
+  // column perm[i] of B^{-1} = U^{-1} L^{-1} e_i; adj(B) = det(B) B^{-1}
+  for (int i = 0; i < M; i++) {
+    dev::cd w[MC];
+    for (int p = 0; p < M; p++) {
+      if (p < i) {
+        w[p] = make_double2(0.0, 0.0);
+      } else if (p == i) {
+        w[p] = make_double2(1.0, 0.0);
+      } else {
+        dev::cd s = dev::cneg(B[p][i]);
+        for (int q = i + 1; q < p; q++) s = dev::cfms(B[p][q], w[q], s);
+        w[p] = s;
+      }
+    }
+    for (int p = M - 1; p >= 0; p--) {
+      dev::cd s = w[p];
+      for (int q = p + 1; q < M; q++) s = dev::cfms(B[p][q], w[q], s);
+      w[p] = dev::cmul(s, rc[p]);
+    }
+    for (int u = 0; u < M; u++) K[u * M + perm[i]] = dev::cmul(sd, w[u]);
+  }
+  K[M * M] = sd;
+}
+
 }  // namespace fwd
+
+template <int NCMAX>
+cudaError_t launch_kfac_nc(const FwdArgs& a, int64_t n_fam, cudaStream_t s) {
+  const int64_t threads = n_fam * a.n_q * a.F;
+  if (threads == 0) return cudaSuccess;
+  fwd::kfac_kernel<NCMAX><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a, n_fam);
+  return cudaGetLastError();
+}
+
+// Persistent batched launch: blocks pull (correlator, family, tile) items from a list
+// ordered by decreasing cost through one atomic counter; each item's partial goes to its
+// own slot (see batch.cu).
+template <int NCMAX>
+__global__ void __launch_bounds__(128) batch_kernel(const FwdArgs* __restrict__ desc,
+                                                    const BatchItem* __restrict__ items,
+                                                    int64_t n_items, unsigned long long* head,
+                                                    const int64_t* __restrict__ part_off,
+                                                    double2* __restrict__ partials) {
+  extern __shared__ double2 smem[];
+  __shared__ int64_t s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(head, 1ull);
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it >= n_items) break;
+    const BatchItem bi = items[it];
+    const FwdArgs& a = desc[bi.corr];
+    fwd::fwd_item<NCMAX>(a, bi.W, bi.tile, smem,
+                    &partials[part_off[bi.corr] + (int64_t)bi.W * a.n_tiles + bi.tile]);
+    __syncthreads();
+  }
+}
+
+template <int NCMAX>
+cudaError_t launch_batch_nc(int grid, int T, size_t smem, cudaStream_t s, const FwdArgs* desc,
+                            const BatchItem* items, int64_t n_items, unsigned long long* head,
+                            const int64_t* part_off, double2* partials) {
+  // the shared-memory limit was raised by batch_occupancy_nc, outside any stream capture
+  batch_kernel<NCMAX><<<grid, T, smem, s>>>(desc, items, n_items, head, part_off, partials);
+  return cudaGetLastError();
+}
+
+template <int NCMAX>
+int batch_occupancy_nc(int T, size_t smem) {
+  int nb = 0, dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, batch_kernel<NCMAX>) == cudaSuccess) optin -= (int)fa.sharedSizeBytes;
+  cudaFuncSetAttribute(batch_kernel<NCMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<NCMAX>, T, smem) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
 
 template <int NCMAX>
 cudaError_t launch_fwd_nc(const FwdArgs& a, int tile, int64_t items, size_t smem, cudaStream_t s) {

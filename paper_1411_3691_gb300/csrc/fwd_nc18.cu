@@ -14,4 +14,16 @@ cudaError_t launch_pairs_nc18(const FwdArgs& a, int64_t n_pairs, int64_t n_src, 
   return launch_pairs_nc<18>(a, n_pairs, n_src, ii, jj, src_member, mem_family, dets, path, s);
 }
 
+cudaError_t launch_batch_nc18(int grid, int T, size_t smem, cudaStream_t s, const FwdArgs* desc,
+                               const BatchItem* items, int64_t n_items, unsigned long long* head,
+                               const int64_t* part_off, double2* partials) {
+  return launch_batch_nc<18>(grid, T, smem, s, desc, items, n_items, head, part_off, partials);
+}
+
+int batch_occupancy_nc18(int T, size_t smem) { return batch_occupancy_nc<18>(T, smem); }
+
+cudaError_t launch_kfac_nc18(const FwdArgs& a, int64_t n_fam, cudaStream_t s) {
+  return launch_kfac_nc<18>(a, n_fam, s);
+}
+
 }  // namespace mhc

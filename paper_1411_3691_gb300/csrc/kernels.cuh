@@ -34,6 +34,19 @@ struct FwdArgs {
   const double* w_snk;
   double2* partials;         // [items]
   unsigned long long* counters;
+  // two-sided update; snk_orig == nullptr selects the one-sided update with the sinks
+  // in their own order and labels from snk_lab
+  const int32_t* snk_pos;    // [n_snk][Tn] aligned column labels of the sink at position j
+  const int32_t* snk_orig;   // [n_snk] original sink index at position j
+  const int32_t* snk_par;    // [n_snk] bit f: column-permutation parity
+  const int32_t* snk_q;      // [n_snk] sink family of position j
+  const int32_t* q_two;      // [Q] 1: the family uses adj(B)
+  const int32_t* q_off;      // [Q + 1] first position of each sink family
+  const double2* kbuf;       // [W][Q][kstride]: per flavour adj(B) row-major, then det(B)
+  int32_t* kguard;           // [W][Q][F] 1: the block's pivot guard fired
+  int64_t n_q;
+  int kstride;
+  int koff[MHC_FMAX];
 };
 
 namespace dev {
@@ -87,6 +100,21 @@ __device__ __forceinline__ cd dispatch_member(int n, int rho, const cd* S, int L
 }
 
 template <int NCMAX>
+__device__ __forceinline__ void dispatch_kapply(int n, const cd* S, int L, const int32_t* arow,
+                                                const int32_t* col, const cd* K, cd* Y, int ys,
+                                                int* ey) {
+  switch (n) {
+    case 1: kapply<1, 1>(S, L, 1, arow, col, K, Y, ys, ey); return;
+    case 2: kapply<2, 2>(S, L, 2, arow, col, K, Y, ys, ey); return;
+    case 3: kapply<3, 3>(S, L, 3, arow, col, K, Y, ys, ey); return;
+    case 4: kapply<4, 4>(S, L, 4, arow, col, K, Y, ys, ey); return;
+    case 5: kapply<5, 5>(S, L, 5, arow, col, K, Y, ys, ey); return;
+    case 6: kapply<6, 6>(S, L, 6, arow, col, K, Y, ys, ey); return;
+    default: kapply<NCMAX, 0>(S, L, n, arow, col, K, Y, ys, ey); return;
+  }
+}
+
+template <int NCMAX>
 __device__ __forceinline__ cd dispatch_fresh(int n, const cd* S, int L, const int32_t* rows,
                                              const int32_t* col) {
 #define MHC_FD(N) \
@@ -133,13 +161,18 @@ __device__ __forceinline__ bool finite2(double2 v) {
 
 }  // namespace dev
 
+// one work item of the persistent batched launch
+struct BatchItem {
+  int32_t corr, W, tile, pad;
+};
+
 // per-warp refactor queue of the forward kernel
 constexpr int kQueueCap = 64;         // entries per warp
-constexpr int kQueueEntryBytes = 32;  // sizeof(fwd::QEntry)
+constexpr int kQueueEntryBytes = 48;  // sizeof(fwd::QEntry)
 
 // host-side launchers (forward.cu and fwd_nc*.cu)
-cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t items, size_t smem,
-                           double* out, cudaStream_t s);
+cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,
+                           size_t smem, double* out, cudaStream_t s);
 cudaError_t launch_reduce(const double2* partials, int64_t items, double* out, cudaStream_t s);
 cudaError_t launch_pairs(const FwdArgs& a, int ncmax, int64_t n_pairs, int64_t n_src,
                          const int64_t* ii, const int64_t* jj, const int32_t* src_member,
@@ -151,7 +184,13 @@ size_t forward_smem_bytes(int slots, int tile);
   cudaError_t launch_pairs_nc##NC(const FwdArgs& a, int64_t n_pairs, int64_t n_src,           \
                                   const int64_t* ii, const int64_t* jj,                       \
                                   const int32_t* src_member, const int32_t* mem_family,       \
-                                  double* dets, int32_t* path, cudaStream_t s);
+                                  double* dets, int32_t* path, cudaStream_t s);      \
+  cudaError_t launch_batch_nc##NC(int grid, int T, size_t smem, cudaStream_t s,               \
+                                  const FwdArgs* desc, const BatchItem* items,                \
+                                  int64_t n_items, unsigned long long* head,                  \
+                                  const int64_t* part_off, double2* partials);                \
+  int batch_occupancy_nc##NC(int T, size_t smem);                                            \
+  cudaError_t launch_kfac_nc##NC(const FwdArgs& a, int64_t n_fam, cudaStream_t s);
 MHC_DECL_NC(8)
 MHC_DECL_NC(18)
 MHC_DECL_NC(32)

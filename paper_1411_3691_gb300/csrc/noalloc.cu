@@ -102,7 +102,7 @@ extern "C" mhc_status mhc_correlator_noalloc(mhc_plan_t plan, const double* cons
   // needs no clearing between calls.
   a.partials = scratch;
   const size_t smem = forward_smem_bytes(a.slots, tile);
-  cudaError_t e = launch_forward(a, plan_ncmax(p), tile, items, smem, out_dev,
+  cudaError_t e = launch_forward(a, plan_ncmax(p), tile, p.n_fam, items, smem, out_dev,
                                  reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
     set_error(std::string("mhc_correlator_noalloc: launch: ") + cudaGetErrorString(e));

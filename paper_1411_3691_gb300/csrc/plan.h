@@ -32,6 +32,16 @@ struct DevicePlan {
   int32_t* snk_lab = nullptr;    // [n_snk][Tn]
   int32_t* src_member = nullptr; // [n_src] member slot of each source term
   int32_t* mem_family = nullptr; // [n_src] family of each member slot
+  int32_t* snk_order = nullptr;  // two-sided tables (see Plan)
+  int32_t* snk_lab2 = nullptr;
+  int32_t* snk_par2 = nullptr;
+  int32_t* snk_q = nullptr;
+  int32_t* q_off = nullptr;
+  int32_t* q_two = nullptr;
+  double* kbuf = nullptr;        // [W][Q][sum_f ((n_f-1)^2 + 1)] adj(B) and det(B)
+  int32_t* kguard = nullptr;     // [W][Q][F] 1: the block's pivot guard fired
+  int kstride = 0;
+  bool two_sided = false;
   double* w_src = nullptr;       // [n_src] plan weights
   double* w_snk = nullptr;       // [n_snk]
   double* partials = nullptr;    // [items][2] per-work-item partial sums
@@ -76,6 +86,16 @@ struct Plan {
   std::vector<int32_t> src_member;       // [n_src] member slot of each source term
   std::vector<int32_t> mem_family;       // [n_src]
   int max_members = 0;
+  // sink families (two-sided update): sinks in family-major order, columns aligned to
+  // the family's reference with the changed column last in every flavour
+  int64_t n_qfam = 0;
+  std::vector<int32_t> snk_order;        // [n_snk] original sink index at position jj
+  std::vector<int32_t> snk_lab2;         // [n_snk][Tn] aligned column labels
+  std::vector<int32_t> snk_par2;         // [n_snk] bit f: column-permutation parity
+  std::vector<int32_t> snk_q;            // [n_snk] sink family of position jj
+  std::vector<int32_t> q_off;            // [Q+1] first position of each sink family
+  std::vector<int32_t> q_two;            // [Q] 1 when the family uses the two-sided update
+  int64_t two_sided_pairs = 0;           // (family, sink family) blocks using it, x flavours
   int max_n = 0;
   // stats
   mhc_stats stats{};
@@ -91,5 +111,7 @@ mhc_status build_plan(Plan& p);
 double flops_shared_rows(int n, int rho);   // factorise + solve for one (family, sink, flavour)
 double flops_member(int n, int rho);        // one member's det from the cached solve
 double flops_fresh_lu(int n);               // one fresh partial-pivot LU determinant
+double flops_kapply(int n);                 // y = [-adj(B) a; det B] for one sink (two-sided)
+double flops_adjugate(int m);               // adj(B) of one m x m block (two-sided)
 
 }  // namespace mhc

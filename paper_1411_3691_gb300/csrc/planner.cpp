@@ -21,9 +21,10 @@ thread_local std::string g_last_error;
 // Largest bucket of the candidate-pair hash scan that is compared exhaustively; pairs of
 // a longer bucket are compared only within a sliding window of this many terms.
 constexpr size_t kBucketWindow = 2048;
-// Rank-2 adjacency is used for a flavour only when n_f is at least this large: below
-// it two shared rows out of n_f leave too little to share.
-constexpr int kRank2MinN = 6;
+// Rank-2 adjacency is used for a flavour only when n_f is at least this large: below it
+// a rank-2 update (4 dot products per member over n - 2 shared rows) saves too little over
+// splitting the family.
+constexpr int kRank2MinN = 10;
 
 uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
@@ -123,6 +124,24 @@ double flops_member(int n, int rho) {
   return rho == 2 ? 4.0 * dot + 2.0 * 6.0 + 2.0 : dot;
 }
 
+double flops_kapply(int n) {
+  if (n <= 0) return 0.0;
+  const double M = n - 1;
+  return M * (6.0 + 8.0 * (M - 1));  // y[0..M) = -adj(B) a, one row at a time
+}
+
+double flops_adjugate(int m) {
+  if (m <= 0) return 0.0;
+  double f = m * (m + 1) / 2.0;  // pivot measures
+  f += 6.0 * m;                  // reciprocals
+  f += 6.0 * m * (m - 1) / 2.0;  // multipliers
+  for (int k = 0; k < m; k++) f += 8.0 * (m - 1 - k) * (m - 1 - k);  // updates
+  f += 6.0 * (m - 1);            // det(B)
+  for (int i = 0; i < m; i++)    // columns of B^{-1}, scaled by det(B)
+    f += 8.0 * (m - i - 1) * (m - i - 2) / 2.0 + 8.0 * m * (m - 1) / 2.0 + 6.0 * m + 6.0 * m;
+  return f;
+}
+
 double flops_fresh_lu(int n) {
   if (n <= 0) return 0.0;
   double f = n * (n + 1) / 2.0;                  // pivot measures
@@ -133,37 +152,35 @@ double flops_fresh_lu(int n) {
   return f;
 }
 
-mhc_status build_plan(Plan& p) {
-  auto t0 = std::chrono::steady_clock::now();
-  const int F = p.F;
-  const int64_t N = p.n_src;
-  const int Tn = p.Tn;
-  const int rank2 = p.opts.rank2 ? 1 : 0;
-  const int kmax = p.opts.max_family;
-
+// Greedy dominating set of a term graph (Sec. 3): two terms are adjacent when, in every
+// flavour f, their label multisets differ in at most dmax[f] labels.  Candidate pairs come
+// from shared leave-d-out keys of one flavour, then every flavour is checked exactly.
+// Returns the dominated sets (dominator first, then its neighbours ascending).
+std::vector<std::vector<int32_t>> dominated_sets(const std::vector<int32_t>& labels, int64_t N,
+                                                 int F, const std::vector<int32_t>& n_f,
+                                                 const std::vector<int32_t>& off_f, int Tn,
+                                                 const std::vector<int>& dmax, int64_t* n_edges) {
   // ---- per term, per flavour sorted label multisets -------------------------------
-  std::vector<int32_t> sorted(p.labels_src);
+  std::vector<int32_t> sorted(labels);
   for (int64_t i = 0; i < N; i++)
     for (int f = 0; f < F; f++)
-      std::sort(sorted.begin() + i * Tn + p.off_f[f], sorted.begin() + i * Tn + p.off_f[f] + p.n_f[f]);
-  std::vector<int> dmax(F);
-  for (int f = 0; f < F; f++) dmax[f] = (rank2 && p.n_f[f] >= kRank2MinN) ? 2 : 1;
+      std::sort(sorted.begin() + i * Tn + off_f[f], sorted.begin() + i * Tn + off_f[f] + n_f[f]);
 
   // key flavour: the smallest allowed difference, then the largest n
   int f0 = -1;
   for (int f = 0; f < F; f++) {
-    if (p.n_f[f] == 0) continue;
-    if (f0 < 0 || dmax[f] < dmax[f0] || (dmax[f] == dmax[f0] && p.n_f[f] > p.n_f[f0])) f0 = f;
+    if (n_f[f] == 0) continue;
+    if (f0 < 0 || dmax[f] < dmax[f0] || (dmax[f] == dmax[f0] && n_f[f] > n_f[f0])) f0 = f;
   }
 
   // ---- candidate pairs: shared leave-d-out keys of the key flavour ------------------
   std::vector<std::pair<uint64_t, int32_t>> keys;
   if (f0 >= 0) {
-    const int n = p.n_f[f0], d = std::min(dmax[f0], n);
+    const int n = n_f[f0], d = std::min(dmax[f0], n);
     keys.reserve((size_t)N * (d == 1 ? n : n * (n - 1) / 2 + 1));
     std::vector<int32_t> rest;
     for (int64_t i = 0; i < N; i++) {
-      const int32_t* s = &sorted[i * Tn + p.off_f[f0]];
+      const int32_t* s = &sorted[i * Tn + off_f[f0]];
       auto emit = [&](int skip1, int skip2) {
         uint64_t h = 0x9e3779b97f4a7c15ULL;
         for (int m = 0; m < n; m++)
@@ -205,9 +222,9 @@ mhc_status build_plan(Plan& p) {
     const int64_t i = e.first, j = e.second;
     bool ok = true;
     for (int f = 0; f < F && ok; f++) {
-      const int n = p.n_f[f];
+      const int n = n_f[f];
       if (n == 0) continue;
-      const int c = common_sorted(&sorted[i * Tn + p.off_f[f]], &sorted[j * Tn + p.off_f[f]], n);
+      const int c = common_sorted(&sorted[i * Tn + off_f[f]], &sorted[j * Tn + off_f[f]], n);
       ok = (n - c) <= dmax[f];
     }
     if (ok) {
@@ -249,6 +266,24 @@ mhc_status build_plan(Plan& p) {
     dom_sets.push_back(std::move(fam));
   }
   adj.clear();
+
+  *n_edges = edges;
+  return dom_sets;
+}
+
+mhc_status build_plan(Plan& p) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int F = p.F;
+  const int64_t N = p.n_src;
+  const int Tn = p.Tn;
+  const int rank2 = p.opts.rank2 ? 1 : 0;
+  const int kmax = p.opts.max_family;
+
+  std::vector<int> dmax(F);
+  for (int f = 0; f < F; f++) dmax[f] = (rank2 && p.n_f[f] >= kRank2MinN) ? 2 : 1;
+  int64_t edges = 0;
+  std::vector<std::vector<int32_t>> dom_sets =
+      dominated_sets(p.labels_src, N, F, p.n_f, p.off_f, Tn, dmax, &edges);
 
   // ---- work families: align members, group by compatible changed rows ---------------
   p.fam_off.assign(1, 0);
@@ -366,6 +401,85 @@ mhc_status build_plan(Plan& p) {
     }
   }
 
+  // ---- sink families for the two-sided update (Sec. 2: a sink term that differs in one
+  // label changes one column; the same greedy dominating set on the sink side) ---------
+  {
+    std::vector<int> dmax1(F, 1);
+    int64_t sedges = 0;
+    std::vector<std::vector<int32_t>> sink_sets =
+        p.opts.one_sided ? std::vector<std::vector<int32_t>>()
+                           : dominated_sets(p.labels_snk, p.n_snk, F, p.n_f, p.off_f, Tn, dmax1, &sedges);
+    if (p.opts.one_sided)
+      for (int64_t j = 0; j < p.n_snk; j++) sink_sets.push_back({(int32_t)j});
+    struct SGroup {
+      std::vector<int> s;  // per flavour: changed column, -1 = none yet
+      std::vector<int32_t> members;
+      int32_t ref;
+    };
+    std::vector<SGroup> groups;
+    for (auto& ds : sink_sets) {
+      const int32_t v = ds[0];
+      const int32_t* ref = &p.labels_snk[(int64_t)v * Tn];
+      std::vector<SGroup> local;
+      for (int32_t t : ds) {
+        std::vector<int> ch(F, -1);
+        for (int f = 0; f < F; f++) {
+          Align al = align(ref + p.off_f[f], &p.labels_snk[(int64_t)t * Tn + p.off_f[f]], p.n_f[f]);
+          if (!al.changed.empty()) ch[f] = al.changed[0];
+        }
+        bool placed = false;
+        for (auto& g : local) {
+          if ((int)g.members.size() >= 32) continue;
+          bool ok = true;
+          for (int f = 0; f < F && ok; f++) ok = ch[f] < 0 || g.s[f] < 0 || ch[f] == g.s[f];
+          if (!ok) continue;
+          for (int f = 0; f < F; f++)
+            if (g.s[f] < 0) g.s[f] = ch[f];
+          g.members.push_back(t);
+          placed = true;
+          break;
+        }
+        if (!placed) local.push_back(SGroup{ch, {t}, v});
+      }
+      for (auto& g : local) groups.push_back(std::move(g));
+    }
+    // families with at least two sinks use the two-sided update and come first
+    std::stable_partition(groups.begin(), groups.end(), [](const SGroup& g) { return g.members.size() >= 2; });
+    p.snk_order.clear();
+    p.snk_lab2.clear();
+    p.snk_par2.clear();
+    p.snk_q.clear();
+    p.q_off.assign(1, 0);
+    p.q_two.clear();
+    for (auto& g : groups) {
+      const int32_t Q = (int32_t)p.q_two.size();
+      const int32_t* ref = &p.labels_snk[(int64_t)g.ref * Tn];
+      for (int32_t t : g.members) {
+        int bits = 0;
+        std::vector<int32_t> lab(Tn);
+        for (int f = 0; f < F; f++) {
+          const int n = p.n_f[f];
+          if (n == 0) continue;
+          Align al = align(ref + p.off_f[f], &p.labels_snk[(int64_t)t * Tn + p.off_f[f]], n);
+          const int sc = g.s[f] >= 0 ? g.s[f] : n - 1;
+          std::vector<int> order;
+          for (int m = 0; m < n; m++)
+            if (m != sc) order.push_back(m);
+          order.push_back(sc);
+          for (int m = 0; m < n; m++) lab[p.off_f[f] + m] = al.aligned[order[m]];
+          bits |= (al.parity ^ perm_parity(order)) << f;
+        }
+        p.snk_order.push_back(t);
+        p.snk_lab2.insert(p.snk_lab2.end(), lab.begin(), lab.end());
+        p.snk_par2.push_back(bits);
+        p.snk_q.push_back(Q);
+      }
+      p.q_off.push_back((int32_t)p.snk_order.size());
+      p.q_two.push_back(g.members.size() >= 2 ? 1 : 0);
+    }
+    p.n_qfam = (int64_t)p.q_two.size();
+  }
+
   // ---- statistics -------------------------------------------------------------------
   mhc_stats& s = p.stats;
   std::memset(&s, 0, sizeof(s));
@@ -378,15 +492,32 @@ mhc_status build_plan(Plan& p) {
   s.rank2_family_flavours = rank2_blocks;
   s.members = (int64_t)p.mem_term.size();
   s.graph_edges = edges;
+  s.sink_families = p.n_qfam;
   double fl = 0.0;
+  int64_t two_q_sinks = 0, two_q = 0;
+  for (int64_t Q = 0; Q < p.n_qfam; Q++)
+    if (p.q_two[Q]) {
+      two_q++;
+      two_q_sinks += p.q_off[Q + 1] - p.q_off[Q];
+    }
+  int64_t two_blocks = 0;
   for (int64_t W = 0; W < p.n_fam; W++) {
     const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
     for (int f = 0; f < F; f++) {
       const int n = p.n_f[f], rho = p.fam_rank[W * F + f];
       if (n == 0) continue;
-      fl += (double)p.n_snk * (flops_shared_rows(n, rho) + k * flops_member(n, rho));
+      fl += (double)p.n_snk * k * flops_member(n, rho);
+      if (rho == 1) {
+        fl += (double)two_q * flops_adjugate(n - 1) + (double)two_q_sinks * flops_kapply(n) +
+              (double)(p.n_snk - two_q_sinks) * flops_shared_rows(n, 1);
+        two_blocks += two_q;
+      } else {
+        fl += (double)p.n_snk * flops_shared_rows(n, rho);
+      }
     }
   }
+  p.two_sided_pairs = two_blocks;
+  s.two_sided_blocks = two_blocks;
   int Fa = 0;
   for (int f = 0; f < F; f++) Fa += p.n_f[f] > 0;
   const double combine = 6.0 * std::max(Fa - 1, 0) + 1.0 + 4.0;  // flavour product, w_i w_j, accumulate
@@ -541,6 +672,22 @@ mhc_status mhc_plan_families(mhc_plan_t plan, int64_t* n_families, int64_t* fam_
   if (member_term) std::copy(p.mem_term.begin(), p.mem_term.end(), member_term);
   if (member_sign) std::copy(p.mem_sign.begin(), p.mem_sign.end(), member_sign);
   if (member_labels) std::copy(p.mem_lab.begin(), p.mem_lab.end(), member_labels);
+  return MHC_OK;
+}
+
+mhc_status mhc_plan_sinks(mhc_plan_t plan, int64_t* n_sink_families, int32_t* order,
+                          int32_t* labels, int32_t* parity, int32_t* family, int32_t* two_sided) {
+  if (!plan || !n_sink_families) {
+    set_error("mhc_plan_sinks: NULL argument");
+    return MHC_EINVAL;
+  }
+  const Plan& p = *reinterpret_cast<const Plan*>(plan);
+  *n_sink_families = p.n_qfam;
+  if (order) std::copy(p.snk_order.begin(), p.snk_order.end(), order);
+  if (labels) std::copy(p.snk_lab2.begin(), p.snk_lab2.end(), labels);
+  if (parity) std::copy(p.snk_par2.begin(), p.snk_par2.end(), parity);
+  if (family) std::copy(p.snk_q.begin(), p.snk_q.end(), family);
+  if (two_sided) std::copy(p.q_two.begin(), p.q_two.end(), two_sided);
   return MHC_OK;
 }
 

@@ -42,7 +42,8 @@ mhc_status upload(T** dst, const T* src, size_t count) {
 void free_device(DevicePlan& d) {
   void* ptrs[] = {d.fam_info, d.fam_rank, d.fam_arow, d.mem_term, d.mem_par, d.mem_lab,
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
-                  d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk};
+                  d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
+                  d.snk_par2, d.snk_q, d.q_off, d.q_two, d.kbuf, d.kguard};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& bi : d.bwd_index) {
@@ -110,6 +111,22 @@ mhc_status ensure_device(Plan& p) {
   if ((st = upload(&d.mem_family, p.mem_family.data(), p.mem_family.size())) != MHC_OK) return st;
   if ((st = upload(&d.w_src, p.w_src.data(), p.w_src.size())) != MHC_OK) return st;
   if ((st = upload(&d.w_snk, p.w_snk.data(), p.w_snk.size())) != MHC_OK) return st;
+  // two-sided update: sink tables and the adj(B) store (skipped above 16 GB)
+  size_t kstride = 0;
+  for (int f = 0; f < p.F; f++) kstride += p.n_f[f] > 0 ? (size_t)(p.n_f[f] - 1) * (p.n_f[f] - 1) + 1 : 0;
+  const double kbytes = (double)p.n_fam * (double)p.n_qfam * (double)kstride * 16.0;
+  d.two_sided = !p.opts.one_sided && p.two_sided_pairs > 0 && kbytes <= 16e9;
+  if (d.two_sided) {
+    if ((st = upload(&d.snk_order, p.snk_order.data(), p.snk_order.size())) != MHC_OK) return st;
+    if ((st = upload(&d.snk_lab2, p.snk_lab2.data(), p.snk_lab2.size())) != MHC_OK) return st;
+    if ((st = upload(&d.snk_par2, p.snk_par2.data(), p.snk_par2.size())) != MHC_OK) return st;
+    if ((st = upload(&d.snk_q, p.snk_q.data(), p.snk_q.size())) != MHC_OK) return st;
+    if ((st = upload(&d.q_off, p.q_off.data(), p.q_off.size())) != MHC_OK) return st;
+    if ((st = upload(&d.q_two, p.q_two.data(), p.q_two.size())) != MHC_OK) return st;
+    if ((st = upload<double>(&d.kbuf, nullptr, 2 * (size_t)p.n_fam * p.n_qfam * kstride)) != MHC_OK) return st;
+    if ((st = upload<int32_t>(&d.kguard, nullptr, (size_t)p.n_fam * p.n_qfam * p.F)) != MHC_OK) return st;
+    d.kstride = (int)kstride;
+  }
   d.tile = plan_tile(p);
   d.n_tiles = (int32_t)((p.n_snk + d.tile - 1) / d.tile);
   d.n_items = p.n_fam * d.n_tiles;
@@ -152,6 +169,22 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
   a.w_snk = w_snk ? w_snk : p.dev.w_snk;
   a.partials = reinterpret_cast<double2*>(p.dev.partials);
   a.counters = p.dev.counters;
+  if (p.dev.two_sided) {
+    a.snk_pos = p.dev.snk_lab2;
+    a.snk_orig = p.dev.snk_order;
+    a.snk_par = p.dev.snk_par2;
+    a.snk_q = p.dev.snk_q;
+    a.q_two = p.dev.q_two;
+    a.q_off = p.dev.q_off;
+    a.kbuf = reinterpret_cast<const double2*>(p.dev.kbuf);
+    a.kguard = p.dev.kguard;
+    a.n_q = p.n_qfam;
+    a.kstride = p.dev.kstride;
+    for (int f = 0, o = 0; f < p.F; f++) {
+      a.koff[f] = o;
+      o += p.n_f[f] > 0 ? (p.n_f[f] - 1) * (p.n_f[f] - 1) + 1 : 0;
+    }
+  }
   return MHC_OK;
 }
 
@@ -192,7 +225,7 @@ mhc_status mhc_correlator(mhc_plan_t plan, const double* const* S_f, const doubl
   if ((st = fill_fwd_args(p, S_f, w_src_dev, w_snk_dev, a)) != MHC_OK) return st;
   const int tile = p.dev.tile;
   const size_t smem = forward_smem_bytes(a.slots, tile);
-  MHC_CUDA(launch_forward(a, plan_ncmax(p), tile, p.dev.n_items, smem, out_dev,
+  MHC_CUDA(launch_forward(a, plan_ncmax(p), tile, p.n_fam, p.dev.n_items, smem, out_dev,
                           reinterpret_cast<cudaStream_t>(stream)));
   return MHC_OK;
 }

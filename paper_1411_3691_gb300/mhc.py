@@ -26,7 +26,7 @@ MHC_NMAX = 32
 MHC_FMAX = 8
 
 EXPORTED = ["mhc_last_error", "mhc_plan_opts_default", "mhc_plan", "mhc_plan_destroy",
-            "mhc_plan_stats", "mhc_plan_families", "mhc_correlator", "mhc_correlator_noalloc",
+            "mhc_plan_stats", "mhc_plan_families", "mhc_plan_sinks", "mhc_correlator", "mhc_correlator_noalloc",
             "mhc_correlator_backward",
             "mhc_pair_dets", "mhc_get_status", "mhc_batch_create", "mhc_batch_destroy",
             "mhc_batch_correlator", "mhc_batch_info", "mhc_fp64_peak"]
@@ -41,7 +41,8 @@ class MHCError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("tau_parent", ctypes.c_double), ("tau_child", ctypes.c_double),
                 ("sink_tile", ctypes.c_int32), ("rank2", ctypes.c_int32),
-                ("max_family", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("max_family", ctypes.c_int32), ("one_sided", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -51,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("graph_edges", ctypes.c_int64), ("flops_per_call", ctypes.c_double),
                 ("fresh_lu_flops_per_pair", ctypes.c_double), ("bytes_per_call", ctypes.c_double),
                 ("plan_seconds", ctypes.c_double), ("refactor_parent", ctypes.c_int64),
-                ("refactor_child", ctypes.c_int64), ("reserved", ctypes.c_int64 * 6)]
+                ("refactor_child", ctypes.c_int64), ("sink_families", ctypes.c_int64),
+                ("two_sided_blocks", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -80,6 +82,7 @@ def lib():
         L.mhc_plan_destroy.restype = None
         L.mhc_plan_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.mhc_plan_families.argtypes = [_vp, _i64p, _i64p, _i32p, _i32p, _i32p, _i64p, _i32p, _i32p]
+        L.mhc_plan_sinks.argtypes = [_vp, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p]
         L.mhc_correlator.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp]
         L.mhc_correlator_noalloc.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _vp, _vp, _vp]
         L.mhc_correlator_backward.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _vp, _vp,
@@ -186,6 +189,20 @@ def mhc_plan_families(plan, F: int, Tn: int, n_src: int) -> dict:
                                sign.ctypes.data_as(_i32p), labs.ctypes.data_as(_i32p)))
     return {"offset": off, "rank": rank, "rows": rows, "ref": ref, "term": term, "sign": sign,
             "labels": labs}
+
+
+def mhc_plan_sinks(plan, Tn: int, n_snk: int) -> dict:
+    nQ = ctypes.c_int64()
+    L = lib()
+    _check(L.mhc_plan_sinks(_vp(plan), ctypes.byref(nQ), None, None, None, None, None))
+    order = np.zeros(n_snk, np.int32)
+    labels = np.zeros((n_snk, Tn), np.int32)
+    parity = np.zeros(n_snk, np.int32)
+    family = np.zeros(n_snk, np.int32)
+    two = np.zeros(nQ.value, np.int32)
+    _check(L.mhc_plan_sinks(_vp(plan), ctypes.byref(nQ), order.ctypes.data_as(_i32p), labels.ctypes.data_as(_i32p),
+                            parity.ctypes.data_as(_i32p), family.ctypes.data_as(_i32p), two.ctypes.data_as(_i32p)))
+    return {"order": order, "labels": labels, "parity": parity, "family": family, "two_sided": two}
 
 
 def mhc_correlator(plan, S, w_src=None, w_snk=None, out=None, stream=None):
@@ -297,6 +314,9 @@ class Plan:
 
     def families(self):
         return mhc_plan_families(self.handle, self.F, self.Tn, self.n_src)
+
+    def sinks(self):
+        return mhc_plan_sinks(self.handle, self.Tn, self.n_snk)
 
     def correlator(self, S, w_src=None, w_snk=None, out=None, stream=None):
         return mhc_correlator(self.handle, S, w_src, w_snk, out, stream)

@@ -226,3 +226,48 @@ def test_flop_count_below_fresh_lu(M):
     st = plan.stats()
     per_pair = st["flops_per_call"] / (plan.n_src * plan.n_snk)
     assert 0 < per_pair < st["fresh_lu_flops_per_pair"] / 4
+
+
+@pytest.mark.parametrize("name", ["helium4", "mixed"])
+def test_sink_families_two_sided(M, name):
+    """Sink-side families: every position's aligned columns give the same determinant as
+    the original columns up to the recorded parity; the members of a two-sided family share
+    their first n_f - 1 columns; and the Schur-complement form det G = alpha det B -
+    g^T adj(B) a of the two-sided update reproduces LAPACK's determinant."""
+    if name == "helium4":
+        w = wl.helium4(scale=3 / 256)
+        w.labels_src, w.w_src = w.labels_src[:20], w.w_src[:20]
+    else:
+        w = wl.make_workload("mixed2", [3, 0, 5], [24, 5, 30], [4, 2], [6, 1, 5, 3, 2], seed=19)
+    plan = M.Plan.from_workload(w)
+    sk = plan.sinks()
+    off = np.cumsum([0] + w.n_f)
+    assert sorted(sk["order"].tolist()) == list(range(plan.n_snk))
+    assert plan.stats()["sink_families"] == len(sk["two_sided"])
+    rng = np.random.default_rng(4)
+    for pos in range(plan.n_snk):
+        j = sk["order"][pos]
+        for f, n in enumerate(w.n_f):
+            if n == 0:
+                continue
+            i = rng.integers(plan.n_src)
+            rows = w.labels_src[i, off[f]:off[f] + n]
+            orig = np.linalg.det(w.S[f][np.ix_(rows, w.labels_snk[j, off[f]:off[f] + n])])
+            cols = sk["labels"][pos, off[f]:off[f] + n]
+            al = np.linalg.det(w.S[f][np.ix_(rows, cols)])
+            sign = -1 if (sk["parity"][pos] >> f) & 1 else 1
+            assert abs(orig - sign * al) <= 1e-12 * (abs(orig) + 1)
+            # Schur complement with the shared columns of the family
+            G = w.S[f][np.ix_(rows, cols)]
+            B, a, g, alpha = G[:-1, :-1], G[:-1, -1], G[-1, :-1], G[-1, -1]
+            adjB = np.linalg.det(B) * np.linalg.inv(B) if n > 1 else np.ones((0, 0))
+            schur = alpha * (np.linalg.det(B) if n > 1 else 1.0) - (g @ adjB @ a if n > 1 else 0.0)
+            assert abs(schur - al) <= 1e-11 * (abs(al) + 1)
+    for Q in range(len(sk["two_sided"])):
+        pos = np.where(sk["family"] == Q)[0]
+        assert (len(pos) >= 2) == bool(sk["two_sided"][Q])
+        for f, n in enumerate(w.n_f):
+            if n > 1:
+                shared = sk["labels"][pos][:, off[f]:off[f] + n - 1]
+                assert np.all(shared == shared[0])
+    plan.close()
