@@ -97,6 +97,7 @@ struct mhc_batch_s {
   double** d_outs = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<FwdArgs> h_desc;    // host copies of the descriptors (for the adj(B) launches)
   std::vector<const void*> key;  // S and out pointers the graph was captured with
   std::vector<double> tune_ms;   // measured time per candidate tile (32, 64, 128)
 };
@@ -158,7 +159,6 @@ mhc_status fill_descs(mhc_batch_s& b, const BatchShape& sh, const double* const*
   for (int k = 0; k < b.count; k++) {
     mhc_status st = fill_fwd_args(*b.plans[k], S[k], nullptr, nullptr, desc[k]);
     if (st != MHC_OK) return st;
-    desc[k].snk_orig = nullptr;  // the batched launch takes the one-sided update
     desc[k].n_tiles = sh.n_tiles[k];
   }
   return MHC_OK;
@@ -186,6 +186,15 @@ mhc_status upload_shape(mhc_batch_s& b, const BatchShape& sh) {
 cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.d_head, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  // two-sided update: adj(B) of every (family, sink family) block of every correlator
+  for (int k = 0; k < b.count; k++) {
+    const FwdArgs& a = b.h_desc[k];
+    if (!a.snk_orig) continue;
+    const int nc = plan_ncmax(*b.plans[k]);
+    e = nc <= 8 ? launch_kfac_nc8(a, b.plans[k]->n_fam, s)
+                : (nc <= 18 ? launch_kfac_nc18(a, b.plans[k]->n_fam, s) : launch_kfac_nc32(a, b.plans[k]->n_fam, s));
+    if (e != cudaSuccess) return e;
+  }
   if (sh.ncmax <= 8)
     e = launch_batch_nc8(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
   else if (sh.ncmax <= 18)
@@ -286,6 +295,7 @@ mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* p
     std::vector<FwdArgs> desc;
     if ((st = fill_descs(*b, sh, S.data(), desc)) != MHC_OK) break;
     cudaMemcpy(b->d_desc, desc.data(), sizeof(FwdArgs) * count, cudaMemcpyHostToDevice);
+    b->h_desc = desc;
     if ((st = upload_shape(*b, sh)) != MHC_OK) break;
     float ms = 0.f;
     for (int rep = 0; rep < 2; rep++) {
@@ -347,6 +357,7 @@ mhc_status mhc_batch_correlator(mhc_batch_t batch, const double* const* const* S
     std::vector<FwdArgs> desc;
     mhc_status st = fill_descs(b, b.shape, S, desc);
     if (st != MHC_OK) return st;
+    b.h_desc = desc;
     if (cudaStreamSynchronize(b.cap) != cudaSuccess ||
         cudaMemcpy(b.d_desc, desc.data(), sizeof(FwdArgs) * b.count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b.d_outs, outs, sizeof(double*) * b.count, cudaMemcpyHostToDevice) != cudaSuccess) {

@@ -95,6 +95,17 @@ __device__ __forceinline__ cd dispatch_member(int n, int rho, const cd* S, int L
       break;
   }
 #undef MHC_MD
+  if constexpr (NCMAX >= 18) {  // the n of the large-nucleus and batched workloads
+    if (n == 9)
+      return rho == 1 ? member_det<9, 9, 1>(S, L, 9, lab, col, Y, ys, ey, kc, fail)
+                      : member_det<9, 9, 2>(S, L, 9, lab, col, Y, ys, ey, kc, fail);
+    if (n == 12)
+      return rho == 1 ? member_det<12, 12, 1>(S, L, 12, lab, col, Y, ys, ey, kc, fail)
+                      : member_det<12, 12, 2>(S, L, 12, lab, col, Y, ys, ey, kc, fail);
+    if (n == 18)
+      return rho == 1 ? member_det<18, 18, 1>(S, L, 18, lab, col, Y, ys, ey, kc, fail)
+                      : member_det<18, 18, 2>(S, L, 18, lab, col, Y, ys, ey, kc, fail);
+  }
   return rho == 1 ? member_det<NCMAX, 0, 1>(S, L, n, lab, col, Y, ys, ey, kc, fail)
                   : member_det<NCMAX, 0, 2>(S, L, n, lab, col, Y, ys, ey, kc, fail);
 }
@@ -110,8 +121,14 @@ __device__ __forceinline__ void dispatch_kapply(int n, const cd* S, int L, const
     case 4: kapply<4, 4>(S, L, 4, arow, col, K, Y, ys, ey); return;
     case 5: kapply<5, 5>(S, L, 5, arow, col, K, Y, ys, ey); return;
     case 6: kapply<6, 6>(S, L, 6, arow, col, K, Y, ys, ey); return;
-    default: kapply<NCMAX, 0>(S, L, n, arow, col, K, Y, ys, ey); return;
+    default: break;
   }
+  if constexpr (NCMAX >= 18) {
+    if (n == 9) { kapply<9, 9>(S, L, 9, arow, col, K, Y, ys, ey); return; }
+    if (n == 12) { kapply<12, 12>(S, L, 12, arow, col, K, Y, ys, ey); return; }
+    if (n == 18) { kapply<18, 18>(S, L, 18, arow, col, K, Y, ys, ey); return; }
+  }
+  kapply<NCMAX, 0>(S, L, n, arow, col, K, Y, ys, ey);
 }
 
 template <int NCMAX>
