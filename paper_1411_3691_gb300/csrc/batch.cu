@@ -97,7 +97,10 @@ struct mhc_batch_s {
   double** d_outs = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<FwdArgs> h_desc;    // host copies of the descriptors (for the adj(B) launches)
+  std::vector<FwdArgs> h_desc;    // host copies of the descriptors
+  int64_t* d_kpref = nullptr;     // [count + 1] first two-sided block thread of each plan
+  int64_t* d_nfam = nullptr;      // [count] families per plan
+  int64_t k_total = 0;
   std::vector<const void*> key;  // S and out pointers the graph was captured with
   std::vector<double> tune_ms;   // measured time per candidate tile (32, 64, 128)
 };
@@ -186,15 +189,15 @@ mhc_status upload_shape(mhc_batch_s& b, const BatchShape& sh) {
 cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.d_head, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  // two-sided update: adj(B) of every (family, sink family) block of every correlator
-  for (int k = 0; k < b.count; k++) {
-    const FwdArgs& a = b.h_desc[k];
-    if (!a.snk_orig) continue;
-    const int nc = plan_ncmax(*b.plans[k]);
-    e = nc <= 8 ? launch_kfac_nc8(a, b.plans[k]->n_fam, s)
-                : (nc <= 18 ? launch_kfac_nc18(a, b.plans[k]->n_fam, s) : launch_kfac_nc32(a, b.plans[k]->n_fam, s));
-    if (e != cudaSuccess) return e;
-  }
+  // two-sided update: the factors of every (family, sink family) block of every
+  // correlator, in one launch
+  if (sh.ncmax <= 8)
+    e = launch_kfac_batch_nc8(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, s);
+  else if (sh.ncmax <= 18)
+    e = launch_kfac_batch_nc18(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, s);
+  else
+    e = launch_kfac_batch_nc32(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, s);
+  if (e != cudaSuccess) return e;
   if (sh.ncmax <= 8)
     e = launch_batch_nc8(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
   else if (sh.ncmax <= 18)
@@ -213,7 +216,8 @@ void destroy(mhc_batch_s* b) {
     cudaDeviceSynchronize();
   }
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  void* ptrs[] = {b->d_desc, b->d_items, b->d_part_off, b->d_partials, b->d_head, b->d_outs};
+  void* ptrs[] = {b->d_desc, b->d_items, b->d_part_off, b->d_partials, b->d_head, b->d_outs,
+                  b->d_kpref, b->d_nfam};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -247,6 +251,21 @@ mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* p
     }
     b->plans.push_back(p);
   }
+  std::vector<int64_t> kpref(1, 0), nfam;
+  for (int k = 0; k < count; k++) {
+    const Plan& p = *b->plans[k];
+    nfam.push_back(p.n_fam);
+    kpref.push_back(kpref.back() + (p.dev.two_sided ? p.n_fam * p.n_qfam * p.F : 0));
+  }
+  b->k_total = kpref.back();
+  if (cudaMalloc(&b->d_kpref, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_nfam, sizeof(int64_t) * count) != cudaSuccess) {
+    destroy(b);
+    set_error("mhc_batch_create: CUDA allocation failed");
+    return MHC_ENOMEM;
+  }
+  cudaMemcpy(b->d_kpref, kpref.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_nfam, nfam.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice);
   if (cudaMalloc(&b->d_desc, sizeof(FwdArgs) * count) != cudaSuccess ||
       cudaMalloc(&b->d_head, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&b->d_outs, sizeof(double*) * count) != cudaSuccess ||

@@ -227,9 +227,11 @@ __device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_
 // Two-sided update: the sink belongs to a sink family whose members share every column but
 // the last, so G = [[B, a], [g^T, alpha]] with B the block of shared rows and shared
 // columns.  By the Schur complement det G = alpha det B - g^T adj(B) a, i.e. det G = g' . y
-// with g' the member's full row and y = [-adj(B) a ; det B].  adj(B) (row-major, then
-// det B) is shared by the whole (family, sink family) block.  Writes y like shared_rows
-// (rank 1) and the member-guard exponent scale to *ey.
+// with g' the member's full row and y = [-det(B) B^{-1} a ; det B].  The block stores the
+// LU factors of B once per (family, sink family) block (P B = L U, U's diagonal replaced by
+// its reciprocals), the row order P as numbers, -det B and det B; each sink then needs two
+// triangular solves.  Writes y like shared_rows (rank 1) and the member-guard scale to *ey.
+//   layout: LU[M][M] | perm[M] (real part) | -det B | det B          (M = n - 1)
 template <int NC, int NFIX>
 __device__ __forceinline__ void kapply(const cd* __restrict__ S, int L, int n_rt,
                                        const int32_t* __restrict__ arow,
@@ -240,22 +242,172 @@ __device__ __forceinline__ void kapply(const cd* __restrict__ S, int L, int n_rt
   const int M = n - 1;
   constexpr int MC = NC - 1 > 0 ? NC - 1 : 1;
   const int cj = colp[M];
-  cd av[MC];
+  cd x[MC];
 #pragma unroll UNR
-  for (int t = 0; t < M; t++) av[t] = ldS(S + (size_t)arow[t] * L + cj);
+  for (int i = 0; i < M; i++) {  // P a, then L^{-1}
+    const int pr = (int)__ldg(&K[M * M + i].x);
+    cd w = ldS(S + (size_t)arow[pr] * L + cj);
+#pragma unroll UNR
+    for (int t = 0; t < i; t++) w = cfms(__ldg(K + i * M + t), x[t], w);
+    x[i] = w;
+  }
+#pragma unroll UNR
+  for (int i = M - 1; i >= 0; i--) {  // U^{-1}
+    cd w = x[i];
+#pragma unroll UNR
+    for (int t = i + 1; t < M; t++) w = cfms(__ldg(K + i * M + t), x[t], w);
+    x[i] = cmul(w, __ldg(K + i * M + i));
+  }
+  const cd nd = __ldg(K + M * M + M);
   int ez = -4096;
 #pragma unroll UNR
   for (int u = 0; u < M; u++) {
-    cd v = cmul(__ldg(K + u * M), av[0]);
-#pragma unroll UNR
-    for (int t = 1; t < M; t++) v = cfma(__ldg(K + u * M + t), av[t], v);
-    const cd y = cneg(v);
+    const cd y = cmul(nd, x[u]);
     Y[u * ys] = y;
     ez = max(ez, expo(y));
   }
-  const cd dB = __ldg(K + M * M);
+  const cd dB = __ldg(K + M * M + M + 1);
   Y[M * ys] = dB;
   *ey = max(ez, expo(dB));
+}
+
+// Two-sided update of a two-row family against a one-column sink family.  The shared rows
+// A (n-2 of them) restricted to the n-1 shared columns are factorised once per block,
+// P A_s = L [U1 | u]; with the free columns ordered last (the last shared column, then the
+// sink's changed column) the null vectors of A = [A_s | a(j)] are
+//   z1 = [-U1^{-1} u ; 1 ; 0]             (the same for every sink of the family)
+//   z2 = [-U1^{-1} L^{-1} P a(j) ; 0 ; 1]
+// and det [A ; b1 ; b2] = sd det(B Z) as in shared_rows with RHO = 2.
+//   layout: LU[M][M] | perm[M] (real part) | -U1^{-1} u [M] | sd      (M = n - 2)
+template <int NC, int NFIX>
+__device__ __forceinline__ void kapply2(const cd* __restrict__ S, int L, int n_rt,
+                                        const int32_t* __restrict__ arow,
+                                        const int32_t* __restrict__ colp, const cd* __restrict__ K,
+                                        cd* __restrict__ Y, int ys, int* ey) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 2;
+  constexpr int MC = NC - 2 > 0 ? NC - 2 : 1;
+  const int cj = colp[n - 1];
+  cd x[MC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+    const int pr = (int)__ldg(&K[M * M + i].x);
+    cd w = ldS(S + (size_t)arow[pr] * L + cj);
+#pragma unroll UNR
+    for (int t = 0; t < i; t++) w = cfms(__ldg(K + i * M + t), x[t], w);
+    x[i] = w;
+  }
+#pragma unroll UNR
+  for (int i = M - 1; i >= 0; i--) {
+    cd w = x[i];
+#pragma unroll UNR
+    for (int t = i + 1; t < M; t++) w = cfms(__ldg(K + i * M + t), x[t], w);
+    x[i] = cmul(w, __ldg(K + i * M + i));
+  }
+  int ez = 0;
+#pragma unroll UNR
+  for (int u = 0; u < M; u++) {
+    const cd v = cneg(x[u]);
+    Y[(n + u) * ys] = v;
+    const cd nu = __ldg(K + M * M + M + u);
+    Y[u * ys] = nu;
+    ez = max(ez, max(expo(v), expo(nu)));
+  }
+  Y[M * ys] = make_double2(1.0, 0.0);
+  Y[(M + 1) * ys] = make_double2(0.0, 0.0);
+  Y[(n + M) * ys] = make_double2(0.0, 0.0);
+  Y[(n + M + 1) * ys] = make_double2(1.0, 0.0);
+  const cd sd = __ldg(K + M * M + 2 * M);
+  Y[2 * n * ys] = sd;
+  *ey = expo(sd) + 2 * ez;
+}
+
+// Factorisation of one two-sided block (see kapply / kapply2), one thread per block: rows
+// S[arow[i]], i < M, columns S[.][scol[u]], u < M (+ the extra column u = M for RHO = 2).
+// Partial pivoting with the shared_rows rule.  Returns true when the pivot guard fires.
+template <int NC, int NFIX, int RHO>
+__device__ __forceinline__ bool kfac_block(const cd* __restrict__ S, int L, int n_rt,
+                                           const int32_t* __restrict__ arow,
+                                           const int32_t* __restrict__ scol, cd* __restrict__ K,
+                                           int kp) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - RHO;
+  constexpr int MC = NC - RHO > 0 ? NC - RHO : 1;
+  const int C = RHO == 2 ? M + 1 : M;  // columns kept
+  cd B[MC][MC + 1];
+  int perm[MC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+    perm[i] = i;
+    const cd* row = S + (size_t)arow[i] * L;
+#pragma unroll UNR
+    for (int u = 0; u < C; u++) B[i][u] = ldS(row + scol[u]);
+  }
+  int parity = 0, emin = 4096, emax = -4096;
+  bool zero = false;
+  cd det = make_double2(1.0, 0.0);
+#pragma unroll UNR
+  for (int k = 0; k < M; k++) {
+    double best = abs1(B[k][k]);
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const double m = abs1(B[i][k]);
+      const bool sw = gt_nonneg(m, best);
+      best = sw ? m : best;
+      parity ^= (int)sw;
+      const int pk = perm[k], pi = perm[i];
+      perm[k] = sw ? pi : pk;
+      perm[i] = sw ? pk : pi;
+#pragma unroll UNR
+      for (int u = 0; u < C; u++) {
+        const cd t = B[k][u];
+        B[k][u] = sw ? B[i][u] : t;
+        B[i][u] = sw ? t : B[i][u];
+      }
+    }
+    const int e = expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    const cd piv = B[k][k];
+    det = (k == 0) ? piv : cmul(det, piv);
+    const cd rc = crcp(piv);
+    B[k][k] = rc;
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const cd l = cmul(B[i][k], rc);
+      B[i][k] = l;
+#pragma unroll UNR
+      for (int u = k + 1; u < C; u++) B[i][u] = cfms(l, B[k][u], B[i][u]);
+    }
+  }
+  if (M > 0 && (zero || emax - emin > kp)) return true;
+  const cd sd = parity ? cneg(det) : det;
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+#pragma unroll UNR
+    for (int u = 0; u < M; u++) K[i * M + u] = B[i][u];
+    K[M * M + i] = make_double2((double)perm[i], 0.0);
+  }
+  if (RHO == 1) {
+    K[M * M + M] = cneg(sd);
+    K[M * M + M + 1] = sd;
+  } else {
+    cd w[MC];  // -U1^{-1} u, u the transformed extra column
+#pragma unroll UNR
+    for (int p = M - 1; p >= 0; p--) {
+      cd s = B[p][M];
+#pragma unroll UNR
+      for (int q = p + 1; q < M; q++) s = cfma(B[p][q], w[q], s);
+      w[p] = cmul(s, cneg(B[p][p]));
+    }
+#pragma unroll UNR
+    for (int i = 0; i < M; i++) K[M * M + M + i] = w[i];
+    K[M * M + 2 * M] = sd;
+  }
+  return false;
 }
 
 // Fresh determinant of one n x n block by LU with partial pivoting (the refactor path):

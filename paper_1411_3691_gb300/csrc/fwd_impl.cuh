@@ -81,10 +81,14 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
     if (n == 0) continue;
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
     const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
-    if (qtwo && rho == 1 && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
-      dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
-                                  a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f],
-                                  Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+    if (qtwo && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+      const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
+      if (rho == 1)
+        dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                    Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+      else
+        dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                     Y + (size_t)a.yoff[f] * T, T, &ey[f]);
     } else {
       const bool g = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
                                                  Y + (size_t)a.yoff[f] * T, T, &ey[f], a.kp);
@@ -235,94 +239,78 @@ __global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pai
   if (path) path[p] = bits;
 }
 
-// adj(B) of every two-sided (family, sink family, flavour) block: one thread per block.
-// B = S[shared rows][shared columns] ((n-1) x (n-1)); LU with partial pivoting (the same
-// pivot rule and guard as shared_rows), then adj(B) = det(B) B^{-1} column by column.
+// One two-sided block (family W, sink family Q, flavour f) of plan a: factorise B
+// (rank-1 family) or the two-row family's shared rows (see kapply2), or nothing.
 template <int NCMAX>
-__global__ void __launch_bounds__(128) kfac_kernel(const FwdArgs a, int64_t n_fam) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_fam * a.n_q * a.F) return;
+__device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_fam) {
   const int f = (int)(t % a.F);
   const int64_t wq = t / a.F;
   const int Q = (int)(wq % a.n_q);
   const int W = (int)(wq / a.n_q);
   const int n = a.n_f[f];
-  if (n == 0 || !a.q_two[Q] || a.fam_rank[(int64_t)W * a.F + f] != 1) return;
-  const int M = n - 1;
-  constexpr int MC = NCMAX - 1;
+  if (n == 0 || !a.q_two[Q]) return;
+  const int rho = a.fam_rank[(int64_t)W * a.F + f];
   const dev::cd* S = a.S[f];
   const int L = a.L_f[f];
   const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
-  dev::cd B[MC][MC];
-  int perm[MC];
-  for (int i = 0; i < M; i++) {
-    perm[i] = i;
-    for (int u = 0; u < M; u++) B[i][u] = dev::ldS(S + (size_t)arow[i] * L + scol[u]);
+  bool g;
+#define MHC_KF(N)                                                                         \
+  case N:                                                                                 \
+    g = rho == 1 ? dev::kfac_block<N, N, 1>(S, L, N, arow, scol, K, a.kp)                 \
+                 : dev::kfac_block<N, N, (N >= 2 ? 2 : 1)>(S, L, N, arow, scol, K, a.kp); \
+    break;
+  switch (n) {
+    MHC_KF(1)
+    MHC_KF(2)
+    MHC_KF(3)
+    MHC_KF(4)
+    MHC_KF(5)
+    MHC_KF(6)
+    default:
+      g = rho == 1 ? dev::kfac_block<NCMAX, 0, 1>(S, L, n, arow, scol, K, a.kp)
+                   : dev::kfac_block<NCMAX, 0, 2>(S, L, n, arow, scol, K, a.kp);
   }
-  int parity = 0, emin = 4096, emax = -4096;
-  bool zero = false;
-  dev::cd rc[MC];
-  dev::cd det = make_double2(1.0, 0.0);
-  for (int k = 0; k < M; k++) {
-    double best = dev::abs1(B[k][k]);
-    for (int i = k + 1; i < M; i++) {
-      const double m = dev::abs1(B[i][k]);
-      if (dev::gt_nonneg(m, best)) {
-        best = m;
-        parity ^= 1;
-        for (int u = 0; u < M; u++) {
-          const dev::cd x = B[k][u];
-          B[k][u] = B[i][u];
-          B[i][u] = x;
-        }
-        const int pi = perm[i];
-        perm[i] = perm[k];
-        perm[k] = pi;
-      }
-    }
-    const int e = dev::expo(best);
-    zero |= (__double_as_longlong(best) == 0);
-    emin = min(emin, e);
-    emax = max(emax, e);
-    det = (k == 0) ? B[k][k] : dev::cmul(det, B[k][k]);
-    rc[k] = dev::crcp(B[k][k]);
-    for (int i = k + 1; i < M; i++) {
-      const dev::cd l = dev::cmul(B[i][k], rc[k]);
-      B[i][k] = l;
-      for (int u = k + 1; u < M; u++) B[i][u] = dev::cfms(l, B[k][u], B[i][u]);
-    }
+#undef MHC_KF
+  a.kguard[t] = g ? 1 : 0;
+}
+
+// two-sided blocks of one plan: one thread per (W, Q, f)
+template <int NCMAX>
+__global__ void __launch_bounds__(128) kfac_kernel(const FwdArgs a, int64_t n_fam) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_fam * a.n_q * a.F) return;
+  kfac_one<NCMAX>(a, t, n_fam);
+}
+
+// two-sided blocks of every plan of a batch in one launch: kpref[k] is the first thread of
+// correlator k (prefix sums of n_fam * n_q * F; kpref[count] = total)
+template <int NCMAX>
+__global__ void __launch_bounds__(128) kfac_batch_kernel(const FwdArgs* __restrict__ desc,
+                                                         const int64_t* __restrict__ kpref,
+                                                         const int64_t* __restrict__ nfam, int count) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kpref[count]) return;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // last k with kpref[k] <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (kpref[mid] <= t) lo = mid; else hi = mid - 1;
   }
-  const bool guard = M > 0 && (zero || emax - emin > a.kp);
-  a.kguard[t] = guard ? 1 : 0;
-  if (guard) return;
-  const dev::cd sd = parity ? dev::cneg(det) : det;
-  // column perm[i] of B^{-1} = U^{-1} L^{-1} e_i; adj(B) = det(B) B^{-1}
-  for (int i = 0; i < M; i++) {
-    dev::cd w[MC];
-    for (int p = 0; p < M; p++) {
-      if (p < i) {
-        w[p] = make_double2(0.0, 0.0);
-      } else if (p == i) {
-        w[p] = make_double2(1.0, 0.0);
-      } else {
-        dev::cd s = dev::cneg(B[p][i]);
-        for (int q = i + 1; q < p; q++) s = dev::cfms(B[p][q], w[q], s);
-        w[p] = s;
-      }
-    }
-    for (int p = M - 1; p >= 0; p--) {
-      dev::cd s = w[p];
-      for (int q = p + 1; q < M; q++) s = dev::cfms(B[p][q], w[q], s);
-      w[p] = dev::cmul(s, rc[p]);
-    }
-    for (int u = 0; u < M; u++) K[u * M + perm[i]] = dev::cmul(sd, w[u]);
-  }
-  K[M * M] = sd;
+  const FwdArgs& a = desc[lo];
+  if (!a.snk_orig) return;
+  kfac_one<NCMAX>(a, t - kpref[lo], nfam[lo]);
 }
 
 }  // namespace fwd
+
+template <int NCMAX>
+cudaError_t launch_kfac_batch_nc(const FwdArgs* desc, const int64_t* kpref, const int64_t* nfam,
+                                 int count, int64_t total, cudaStream_t s) {
+  if (total == 0) return cudaSuccess;
+  fwd::kfac_batch_kernel<NCMAX><<<(unsigned)((total + 127) / 128), 128, 0, s>>>(desc, kpref, nfam, count);
+  return cudaGetLastError();
+}
 
 template <int NCMAX>
 cudaError_t launch_kfac_nc(const FwdArgs& a, int64_t n_fam, cudaStream_t s) {

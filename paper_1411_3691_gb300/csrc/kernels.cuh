@@ -132,6 +132,25 @@ __device__ __forceinline__ void dispatch_kapply(int n, const cd* S, int L, const
 }
 
 template <int NCMAX>
+__device__ __forceinline__ void dispatch_kapply2(int n, const cd* S, int L, const int32_t* arow,
+                                                 const int32_t* col, const cd* K, cd* Y, int ys,
+                                                 int* ey) {
+  switch (n) {
+    case 2: kapply2<2, 2>(S, L, 2, arow, col, K, Y, ys, ey); return;
+    case 3: kapply2<3, 3>(S, L, 3, arow, col, K, Y, ys, ey); return;
+    case 4: kapply2<4, 4>(S, L, 4, arow, col, K, Y, ys, ey); return;
+    case 5: kapply2<5, 5>(S, L, 5, arow, col, K, Y, ys, ey); return;
+    case 6: kapply2<6, 6>(S, L, 6, arow, col, K, Y, ys, ey); return;
+    default: break;
+  }
+  if constexpr (NCMAX >= 18) {
+    if (n == 12) { kapply2<12, 12>(S, L, 12, arow, col, K, Y, ys, ey); return; }
+    if (n == 18) { kapply2<18, 18>(S, L, 18, arow, col, K, Y, ys, ey); return; }
+  }
+  kapply2<NCMAX, 0>(S, L, n, arow, col, K, Y, ys, ey);
+}
+
+template <int NCMAX>
 __device__ __forceinline__ cd dispatch_fresh(int n, const cd* S, int L, const int32_t* rows,
                                              const int32_t* col) {
 #define MHC_FD(N) \
@@ -207,7 +226,10 @@ size_t forward_smem_bytes(int slots, int tile);
                                   int64_t n_items, unsigned long long* head,                  \
                                   const int64_t* part_off, double2* partials);                \
   int batch_occupancy_nc##NC(int T, size_t smem);                                            \
-  cudaError_t launch_kfac_nc##NC(const FwdArgs& a, int64_t n_fam, cudaStream_t s);
+  cudaError_t launch_kfac_nc##NC(const FwdArgs& a, int64_t n_fam, cudaStream_t s);           \
+  cudaError_t launch_kfac_batch_nc##NC(const FwdArgs* desc, const int64_t* kpref,            \
+                                       const int64_t* nfam, int count, int64_t total,         \
+                                       cudaStream_t s);
 MHC_DECL_NC(8)
 MHC_DECL_NC(18)
 MHC_DECL_NC(32)

@@ -111,7 +111,9 @@ mhc_status build_plan(Plan& p);
 double flops_shared_rows(int n, int rho);   // factorise + solve for one (family, sink, flavour)
 double flops_member(int n, int rho);        // one member's det from the cached solve
 double flops_fresh_lu(int n);               // one fresh partial-pivot LU determinant
-double flops_kapply(int n);                 // y = [-adj(B) a; det B] for one sink (two-sided)
-double flops_adjugate(int m);               // adj(B) of one m x m block (two-sided)
+double flops_kapply(int n);                 // y = [-det(B) B^{-1} a; det B] for one sink
+double flops_adjugate(int m);               // LU factors of one m x m two-sided block
+double flops_kapply2(int n);                // z2 for one sink (two-row family)
+double flops_rank2_block(int n);            // LU factors and -U1^{-1}u of one two-row block
 
 }  // namespace mhc

@@ -124,21 +124,40 @@ double flops_member(int n, int rho) {
   return rho == 2 ? 4.0 * dot + 2.0 * 6.0 + 2.0 : dot;
 }
 
+// two-sided update, per sink: P a, forward and backward triangular solves with the stored
+// LU factors of B (M = n - 1), scaling by -det B
 double flops_kapply(int n) {
-  if (n <= 0) return 0.0;
+  if (n <= 1) return 0.0;
   const double M = n - 1;
-  return M * (6.0 + 8.0 * (M - 1));  // y[0..M) = -adj(B) a, one row at a time
+  return 8.0 * M * (M - 1) + 6.0 * M + 6.0 * M;
 }
 
+// LU factors of one M x M block B with partial pivoting (two-sided update, per block)
 double flops_adjugate(int m) {
   if (m <= 0) return 0.0;
   double f = m * (m + 1) / 2.0;  // pivot measures
-  f += 6.0 * m;                  // reciprocals
+  f += 6.0 * m;                  // reciprocals (kept for the solves)
   f += 6.0 * m * (m - 1) / 2.0;  // multipliers
   for (int k = 0; k < m; k++) f += 8.0 * (m - 1 - k) * (m - 1 - k);  // updates
   f += 6.0 * (m - 1);            // det(B)
-  for (int i = 0; i < m; i++)    // columns of B^{-1}, scaled by det(B)
-    f += 8.0 * (m - i - 1) * (m - i - 2) / 2.0 + 8.0 * m * (m - 1) / 2.0 + 6.0 * m + 6.0 * m;
+  return f;
+}
+
+// two-row family, per sink: z2 = -U1^{-1} L^{-1} P a (M = n - 2)
+double flops_kapply2(int n) {
+  if (n < 3) return 0.0;
+  const double M = n - 2;
+  return 8.0 * M * (M - 1) + 6.0 * M;
+}
+
+// two-row family, per block: LU of the M shared rows over M + 1 shared columns, -U1^{-1} u
+double flops_rank2_block(int n) {
+  if (n < 2) return 0.0;
+  const int m = n - 2;
+  double f = m * (m + 1) / 2.0 + 6.0 * m + 6.0 * m * (m - 1) / 2.0;
+  for (int k = 0; k < m; k++) f += 8.0 * (m - 1 - k) * (m - k);
+  f += 6.0 * std::max(m - 1, 0);
+  f += 8.0 * m * (m - 1) / 2.0 + 6.0 * m;
   return f;
 }
 
@@ -510,10 +529,11 @@ mhc_status build_plan(Plan& p) {
       if (rho == 1) {
         fl += (double)two_q * flops_adjugate(n - 1) + (double)two_q_sinks * flops_kapply(n) +
               (double)(p.n_snk - two_q_sinks) * flops_shared_rows(n, 1);
-        two_blocks += two_q;
       } else {
-        fl += (double)p.n_snk * flops_shared_rows(n, rho);
+        fl += (double)two_q * flops_rank2_block(n) + (double)two_q_sinks * flops_kapply2(n) +
+              (double)(p.n_snk - two_q_sinks) * flops_shared_rows(n, rho);
       }
+      two_blocks += two_q;
     }
   }
   p.two_sided_pairs = two_blocks;

@@ -60,6 +60,13 @@ int log2_inv(double tau) {
 
 }  // namespace
 
+// complex entries of one two-sided block of a flavour with n labels (see kapply/kapply2)
+size_t kblock_size(int n) {
+  if (n <= 0) return 0;
+  const size_t m1 = (size_t)(n - 1), m2 = n >= 2 ? (size_t)(n - 2) : 0;
+  return std::max(m1 * m1 + m1 + 2, m2 * m2 + 2 * m2 + 1);
+}
+
 int plan_ncmax(const Plan& p) { return p.max_n <= 8 ? 8 : (p.max_n <= 18 ? 18 : 32); }
 
 int plan_tile(const Plan& p) {
@@ -113,7 +120,7 @@ mhc_status ensure_device(Plan& p) {
   if ((st = upload(&d.w_snk, p.w_snk.data(), p.w_snk.size())) != MHC_OK) return st;
   // two-sided update: sink tables and the adj(B) store (skipped above 16 GB)
   size_t kstride = 0;
-  for (int f = 0; f < p.F; f++) kstride += p.n_f[f] > 0 ? (size_t)(p.n_f[f] - 1) * (p.n_f[f] - 1) + 1 : 0;
+  for (int f = 0; f < p.F; f++) kstride += kblock_size(p.n_f[f]);
   const double kbytes = (double)p.n_fam * (double)p.n_qfam * (double)kstride * 16.0;
   d.two_sided = !p.opts.one_sided && p.two_sided_pairs > 0 && kbytes <= 16e9;
   if (d.two_sided) {
@@ -182,7 +189,7 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
     a.kstride = p.dev.kstride;
     for (int f = 0, o = 0; f < p.F; f++) {
       a.koff[f] = o;
-      o += p.n_f[f] > 0 ? (p.n_f[f] - 1) * (p.n_f[f] - 1) + 1 : 0;
+      o += (int)kblock_size(p.n_f[f]);
     }
   }
   return MHC_OK;
