@@ -410,6 +410,136 @@ __device__ __forceinline__ bool kfac_block(const cd* __restrict__ S, int L, int 
   return false;
 }
 
+// Two-sided update of a one-row family against a two-column sink family: the n-1 shared
+// rows A and the n-2 shared columns give B = A[:, shared] ((n-1) x (n-2)), factorised once
+// per block, P B = L [U1 ; 0].  For a sink with changed columns a1, a2 let
+// at = L^{-1} P a_t = [at_top (n-2) ; at_bot].  The cofactor vector of the member row is
+//   y = sd [ -U1^{-1}(a2_top a1_bot - a1_top a2_bot) ; -a2_bot ; a1_bot ],
+// sd = sign(P) det(U1), with no division by the last pivot a1_bot.
+//   layout: LU[n-1][n-2] (rows < n-2: L below, reciprocal on, U above the diagonal; row
+//           n-2: multipliers) | perm[n-1] (real part) | sd
+template <int NC, int NFIX>
+__device__ __forceinline__ void kapply12(const cd* __restrict__ S, int L, int n_rt,
+                                         const int32_t* __restrict__ arow,
+                                         const int32_t* __restrict__ colp, const cd* __restrict__ K,
+                                         cd* __restrict__ Y, int ys, int* ey) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int C = n - 2, M = n - 1;
+  constexpr int MC = NC - 1 > 0 ? NC - 1 : 1;
+  const int c1 = colp[n - 2], c2 = colp[n - 1];
+  cd x1[MC], x2[MC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {  // P a_t, then L^{-1}
+    const int pr = (int)__ldg(&K[M * C + i].x);
+    const cd* row = S + (size_t)arow[pr] * L;
+    cd w1 = ldS(row + c1), w2 = ldS(row + c2);
+#pragma unroll UNR
+    for (int t = 0; t < i && t < C; t++) {
+      const cd l = __ldg(K + i * C + t);
+      w1 = cfms(l, x1[t], w1);
+      w2 = cfms(l, x2[t], w2);
+    }
+    x1[i] = w1;
+    x2[i] = w2;
+  }
+  const cd b1 = x1[C], b2 = x2[C];
+  cd v[MC];
+#pragma unroll UNR
+  for (int i = 0; i < C; i++) v[i] = cfms(x1[i], b2, cmul(x2[i], b1));
+#pragma unroll UNR
+  for (int i = C - 1; i >= 0; i--) {  // U1^{-1}
+    cd w = v[i];
+#pragma unroll UNR
+    for (int t = i + 1; t < C; t++) w = cfms(__ldg(K + i * C + t), v[t], w);
+    v[i] = cmul(w, __ldg(K + i * C + i));
+  }
+  const cd sd = __ldg(K + M * C + M);
+  const cd nsd = cneg(sd);
+  int ez = -4096;
+#pragma unroll UNR
+  for (int u = 0; u < C; u++) {
+    const cd y = cmul(nsd, v[u]);
+    Y[u * ys] = y;
+    ez = max(ez, expo(y));
+  }
+  const cd yc1 = cmul(nsd, b2), yc2 = cmul(sd, b1);
+  Y[C * ys] = yc1;
+  Y[(C + 1) * ys] = yc2;
+  *ey = max(ez, max(expo(yc1), expo(yc2)));
+}
+
+// Factorisation of a (one-row family, two-column sink family) block (see kapply12): rows
+// S[arow[i]], i < n-1, columns S[.][scol[u]], u < n-2.  Returns true when the pivot guard
+// fires.
+template <int NC, int NFIX>
+__device__ __forceinline__ bool kfac_block12(const cd* __restrict__ S, int L, int n_rt,
+                                             const int32_t* __restrict__ arow,
+                                             const int32_t* __restrict__ scol, cd* __restrict__ K,
+                                             int kp) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 1, C = n - 2;
+  constexpr int MC = NC - 1 > 0 ? NC - 1 : 1;
+  constexpr int CC = NC - 2 > 0 ? NC - 2 : 1;
+  cd B[MC][CC];
+  int perm[MC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+    perm[i] = i;
+    const cd* row = S + (size_t)arow[i] * L;
+#pragma unroll UNR
+    for (int u = 0; u < C; u++) B[i][u] = ldS(row + scol[u]);
+  }
+  int parity = 0, emin = 4096, emax = -4096;
+  bool zero = false;
+  cd det = make_double2(1.0, 0.0);
+#pragma unroll UNR
+  for (int k = 0; k < C; k++) {
+    double best = abs1(B[k][k]);
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const double m = abs1(B[i][k]);
+      const bool sw = gt_nonneg(m, best);
+      best = sw ? m : best;
+      parity ^= (int)sw;
+      const int pk = perm[k], pi = perm[i];
+      perm[k] = sw ? pi : pk;
+      perm[i] = sw ? pk : pi;
+#pragma unroll UNR
+      for (int u = 0; u < C; u++) {
+        const cd t = B[k][u];
+        B[k][u] = sw ? B[i][u] : t;
+        B[i][u] = sw ? t : B[i][u];
+      }
+    }
+    const int e = expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    const cd piv = B[k][k];
+    det = (k == 0) ? piv : cmul(det, piv);
+    const cd rc = crcp(piv);
+    B[k][k] = rc;
+#pragma unroll UNR
+    for (int i = k + 1; i < M; i++) {
+      const cd l = cmul(B[i][k], rc);
+      B[i][k] = l;
+#pragma unroll UNR
+      for (int u = k + 1; u < C; u++) B[i][u] = cfms(l, B[k][u], B[i][u]);
+    }
+  }
+  if (C > 0 && (zero || emax - emin > kp)) return true;
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {
+#pragma unroll UNR
+    for (int u = 0; u < C; u++) K[i * C + u] = B[i][u];
+    K[M * C + i] = make_double2((double)perm[i], 0.0);
+  }
+  K[M * C + M] = parity ? cneg(det) : det;
+  return false;
+}
+
 // Fresh determinant of one n x n block by LU with partial pivoting (the refactor path):
 // rows S[rows[m]], columns col[q].
 template <int NC, int NFIX>

@@ -27,11 +27,6 @@ struct QEntry {
   double pad2;
 };
 
-// column labels of the sink at position j (aligned order in the two-sided update)
-__device__ __forceinline__ const int32_t* sink_cols(const FwdArgs& a, int64_t j) {
-  return (a.snk_orig ? a.snk_pos : a.snk_lab) + j * a.Tn;
-}
-
 template <int NCMAX>
 __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
                               double2& acc) {
@@ -39,7 +34,7 @@ __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int
   if (lane < count) {
     const QEntry e = q[lane];
     const int64_t j = jbase + e.lane;
-    const int32_t* cols = sink_cols(a, j);
+    const int32_t* cols = dev::sink_cols(a, j);
     double2 prod = e.prod;
     int32_t rows[NCMAX];
     for (int f = 0; f < a.F; f++) {
@@ -65,7 +60,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   const int64_t jraw = (int64_t)tile * T + tid;
   const bool valid = jraw < a.n_snk;
   const int64_t j = valid ? jraw : a.n_snk - 1;  // sink position
-  const int32_t* cols = sink_cols(a, j);
+  const int32_t* cols = dev::sink_cols(a, j);
   const int Q = a.snk_orig ? a.snk_q[j] : -1;
   const bool qtwo = Q >= 0 && a.q_two[Q];
   const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
@@ -81,14 +76,18 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
     if (n == 0) continue;
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
     const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
-    if (qtwo && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+    const int sig = qtwo ? a.q_rank[(int64_t)Q * a.F + f] : 0;
+    if (qtwo && (rho == 1 || sig == 1) && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
       const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
-      if (rho == 1)
-        dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                    Y + (size_t)a.yoff[f] * T, T, &ey[f]);
-      else
+      if (rho == 2)
         dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
                                      Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+      else if (sig == 2)
+        dev::dispatch_kapply12<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                      Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+      else
+        dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                    Y + (size_t)a.yoff[f] * T, T, &ey[f]);
     } else {
       const bool g = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
                                                  Y + (size_t)a.yoff[f] * T, T, &ey[f], a.kp);
@@ -250,12 +249,35 @@ __device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_
   const int n = a.n_f[f];
   if (n == 0 || !a.q_two[Q]) return;
   const int rho = a.fam_rank[(int64_t)W * a.F + f];
+  const int sig = a.q_rank[(int64_t)Q * a.F + f];
   const dev::cd* S = a.S[f];
   const int L = a.L_f[f];
   const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
+  if (rho == 2 && sig == 2) {  // two changed rows and columns: one-sided update
+    a.kguard[t] = 1;
+    return;
+  }
   bool g;
+  if (sig == 2) {
+#define MHC_K12(N) \
+  case N:          \
+    g = dev::kfac_block12<N, N>(S, L, N, arow, scol, K, a.kp); \
+    break;
+    switch (n) {
+      MHC_K12(2)
+      MHC_K12(3)
+      MHC_K12(4)
+      MHC_K12(5)
+      MHC_K12(6)
+      default:
+        g = dev::kfac_block12<NCMAX, 0>(S, L, n, arow, scol, K, a.kp);
+    }
+#undef MHC_K12
+    a.kguard[t] = g ? 1 : 0;
+    return;
+  }
 #define MHC_KF(N)                                                                         \
   case N:                                                                                 \
     g = rho == 1 ? dev::kfac_block<N, N, 1>(S, L, N, arow, scol, K, a.kp)                 \

@@ -40,7 +40,8 @@ struct FwdArgs {
   const int32_t* snk_orig;   // [n_snk] original sink index at position j
   const int32_t* snk_par;    // [n_snk] bit f: column-permutation parity
   const int32_t* snk_q;      // [n_snk] sink family of position j
-  const int32_t* q_two;      // [Q] 1: the family uses adj(B)
+  const int32_t* q_two;      // [Q] 1: the family uses the two-sided update
+  const int32_t* q_rank;     // [Q][F] changed columns (1 or 2) of the sink family
   const int32_t* q_off;      // [Q + 1] first position of each sink family
   const double2* kbuf;       // [W][Q][kstride]: per flavour adj(B) row-major, then det(B)
   int32_t* kguard;           // [W][Q][F] 1: the block's pivot guard fired
@@ -151,6 +152,25 @@ __device__ __forceinline__ void dispatch_kapply2(int n, const cd* S, int L, cons
 }
 
 template <int NCMAX>
+__device__ __forceinline__ void dispatch_kapply12(int n, const cd* S, int L, const int32_t* arow,
+                                                  const int32_t* col, const cd* K, cd* Y, int ys,
+                                                  int* ey) {
+  switch (n) {
+    case 2: kapply12<2, 2>(S, L, 2, arow, col, K, Y, ys, ey); return;
+    case 3: kapply12<3, 3>(S, L, 3, arow, col, K, Y, ys, ey); return;
+    case 4: kapply12<4, 4>(S, L, 4, arow, col, K, Y, ys, ey); return;
+    case 5: kapply12<5, 5>(S, L, 5, arow, col, K, Y, ys, ey); return;
+    case 6: kapply12<6, 6>(S, L, 6, arow, col, K, Y, ys, ey); return;
+    default: break;
+  }
+  if constexpr (NCMAX >= 18) {
+    if (n == 12) { kapply12<12, 12>(S, L, 12, arow, col, K, Y, ys, ey); return; }
+    if (n == 18) { kapply12<18, 18>(S, L, 18, arow, col, K, Y, ys, ey); return; }
+  }
+  kapply12<NCMAX, 0>(S, L, n, arow, col, K, Y, ys, ey);
+}
+
+template <int NCMAX>
 __device__ __forceinline__ cd dispatch_fresh(int n, const cd* S, int L, const int32_t* rows,
                                              const int32_t* col) {
 #define MHC_FD(N) \
@@ -168,6 +188,11 @@ __device__ __forceinline__ cd dispatch_fresh(int n, const cd* S, int L, const in
   }
 #undef MHC_FD
   return fresh_det<NCMAX, 0>(S, L, n, rows, col);
+}
+
+// column labels of the sink at position j (aligned order in the two-sided update)
+__device__ __forceinline__ const int32_t* sink_cols(const FwdArgs& a, int64_t j) {
+  return (a.snk_orig ? a.snk_pos : a.snk_lab) + j * a.Tn;
 }
 
 // Rows of member m in flavour f for a fresh factorisation: the shared rows, then the

@@ -38,6 +38,7 @@ struct DevicePlan {
   int32_t* snk_q = nullptr;
   int32_t* q_off = nullptr;
   int32_t* q_two = nullptr;
+  int32_t* q_rank = nullptr;
   double* kbuf = nullptr;        // [W][Q][sum_f ((n_f-1)^2 + 1)] adj(B) and det(B)
   int32_t* kguard = nullptr;     // [W][Q][F] 1: the block's pivot guard fired
   int kstride = 0;
@@ -95,6 +96,7 @@ struct Plan {
   std::vector<int32_t> snk_q;            // [n_snk] sink family of position jj
   std::vector<int32_t> q_off;            // [Q+1] first position of each sink family
   std::vector<int32_t> q_two;            // [Q] 1 when the family uses the two-sided update
+  std::vector<int32_t> q_rank;           // [Q][F] changed columns (1 or 2) per flavour
   int64_t two_sided_pairs = 0;           // (family, sink family) blocks using it, x flavours
   int max_n = 0;
   // stats
@@ -115,5 +117,7 @@ double flops_kapply(int n);                 // y = [-det(B) B^{-1} a; det B] for
 double flops_adjugate(int m);               // LU factors of one m x m two-sided block
 double flops_kapply2(int n);                // z2 for one sink (two-row family)
 double flops_rank2_block(int n);            // LU factors and -U1^{-1}u of one two-row block
+double flops_block12(int n);                // LU factors of one (one-row, two-column) block
+double flops_kapply12(int n);               // y for one sink of a two-column sink family
 
 }  // namespace mhc

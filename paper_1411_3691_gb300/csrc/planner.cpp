@@ -161,6 +161,31 @@ double flops_rank2_block(int n) {
   return f;
 }
 
+// one-row family x two-column sink family, per block: LU of the n-1 shared rows over the
+// n-2 shared columns
+double flops_block12(int n) {
+  if (n < 2) return 0.0;
+  const int m = n - 2, r = n - 1;  // columns, rows
+  double f = 0.0;
+  for (int k = 0; k < m; k++) {
+    f += (r - k);                     // pivot measures
+    f += 6.0;                         // reciprocal
+    f += 6.0 * (r - 1 - k);           // multipliers
+    f += 8.0 * (r - 1 - k) * (m - 1 - k);  // updates
+  }
+  f += 6.0 * std::max(m - 1, 0);      // det(U1)
+  return f;
+}
+
+// one-row family x two-column sink family, per sink: two forward solves over the n-1 rows,
+// the 2 x 2 combination, one backward solve and the scaling (see kapply12)
+double flops_kapply12(int n) {
+  if (n < 2) return 0.0;
+  const double m = n - 2;
+  return 2.0 * 8.0 * (m * (m - 1) / 2.0 + m) + m * (6.0 + 8.0) + 8.0 * m * (m - 1) / 2.0 + 6.0 * m +
+         6.0 * m + 12.0;
+}
+
 double flops_fresh_lu(int n) {
   if (n <= 0) return 0.0;
   double f = n * (n + 1) / 2.0;                  // pivot measures
@@ -421,17 +446,17 @@ mhc_status build_plan(Plan& p) {
   }
 
   // ---- sink families for the two-sided update (Sec. 2: a sink term that differs in one
-  // label changes one column; the same greedy dominating set on the sink side) ---------
+  // label changes one column; the same greedy dominating set on the sink side, with two
+  // changed columns allowed where two changed rows are) ---------------------------------
   {
-    std::vector<int> dmax1(F, 1);
     int64_t sedges = 0;
     std::vector<std::vector<int32_t>> sink_sets =
         p.opts.one_sided ? std::vector<std::vector<int32_t>>()
-                           : dominated_sets(p.labels_snk, p.n_snk, F, p.n_f, p.off_f, Tn, dmax1, &sedges);
+                         : dominated_sets(p.labels_snk, p.n_snk, F, p.n_f, p.off_f, Tn, dmax, &sedges);
     if (p.opts.one_sided)
       for (int64_t j = 0; j < p.n_snk; j++) sink_sets.push_back({(int32_t)j});
     struct SGroup {
-      std::vector<int> s;  // per flavour: changed column, -1 = none yet
+      std::vector<std::vector<int>> R;  // per flavour: changed columns (ascending)
       std::vector<int32_t> members;
       int32_t ref;
     };
@@ -441,19 +466,22 @@ mhc_status build_plan(Plan& p) {
       const int32_t* ref = &p.labels_snk[(int64_t)v * Tn];
       std::vector<SGroup> local;
       for (int32_t t : ds) {
-        std::vector<int> ch(F, -1);
-        for (int f = 0; f < F; f++) {
-          Align al = align(ref + p.off_f[f], &p.labels_snk[(int64_t)t * Tn + p.off_f[f]], p.n_f[f]);
-          if (!al.changed.empty()) ch[f] = al.changed[0];
-        }
+        std::vector<std::vector<int>> ch(F);
+        for (int f = 0; f < F; f++)
+          ch[f] = align(ref + p.off_f[f], &p.labels_snk[(int64_t)t * Tn + p.off_f[f]], p.n_f[f]).changed;
         bool placed = false;
         for (auto& g : local) {
           if ((int)g.members.size() >= 32) continue;
           bool ok = true;
-          for (int f = 0; f < F && ok; f++) ok = ch[f] < 0 || g.s[f] < 0 || ch[f] == g.s[f];
+          std::vector<std::vector<int>> U(F);
+          for (int f = 0; f < F && ok; f++) {
+            std::set<int> u(g.R[f].begin(), g.R[f].end());
+            u.insert(ch[f].begin(), ch[f].end());
+            U[f].assign(u.begin(), u.end());
+            ok = (int)U[f].size() <= dmax[f];
+          }
           if (!ok) continue;
-          for (int f = 0; f < F; f++)
-            if (g.s[f] < 0) g.s[f] = ch[f];
+          g.R = U;
           g.members.push_back(t);
           placed = true;
           break;
@@ -470,9 +498,16 @@ mhc_status build_plan(Plan& p) {
     p.snk_q.clear();
     p.q_off.assign(1, 0);
     p.q_two.clear();
+    p.q_rank.clear();
     for (auto& g : groups) {
       const int32_t Q = (int32_t)p.q_two.size();
       const int32_t* ref = &p.labels_snk[(int64_t)g.ref * Tn];
+      std::vector<std::vector<int>> R(F);
+      for (int f = 0; f < F; f++) {
+        R[f] = g.R[f];
+        if (R[f].empty() && p.n_f[f] > 0) R[f].push_back(p.n_f[f] - 1);
+        p.q_rank.push_back((int32_t)R[f].size());
+      }
       for (int32_t t : g.members) {
         int bits = 0;
         std::vector<int32_t> lab(Tn);
@@ -480,11 +515,11 @@ mhc_status build_plan(Plan& p) {
           const int n = p.n_f[f];
           if (n == 0) continue;
           Align al = align(ref + p.off_f[f], &p.labels_snk[(int64_t)t * Tn + p.off_f[f]], n);
-          const int sc = g.s[f] >= 0 ? g.s[f] : n - 1;
+          // columns: the shared ones (ascending positions), then the changed ones
           std::vector<int> order;
           for (int m = 0; m < n; m++)
-            if (m != sc) order.push_back(m);
-          order.push_back(sc);
+            if (std::find(R[f].begin(), R[f].end(), m) == R[f].end()) order.push_back(m);
+          for (int r : R[f]) order.push_back(r);
           for (int m = 0; m < n; m++) lab[p.off_f[f] + m] = al.aligned[order[m]];
           bits |= (al.parity ^ perm_parity(order)) << f;
         }
@@ -513,12 +548,25 @@ mhc_status build_plan(Plan& p) {
   s.graph_edges = edges;
   s.sink_families = p.n_qfam;
   double fl = 0.0;
-  int64_t two_q_sinks = 0, two_q = 0;
-  for (int64_t Q = 0; Q < p.n_qfam; Q++)
-    if (p.q_two[Q]) {
-      two_q++;
-      two_q_sinks += p.q_off[Q + 1] - p.q_off[Q];
+  // per flavour: two-sided sink families by column rank (count, sinks), one-sided sinks
+  std::vector<int64_t> qc1(F, 0), qs1(F, 0), qc2(F, 0), qs2(F, 0);
+  int64_t one_sinks = 0;
+  for (int64_t Q = 0; Q < p.n_qfam; Q++) {
+    const int64_t sz = p.q_off[Q + 1] - p.q_off[Q];
+    if (!p.q_two[Q]) {
+      one_sinks += sz;
+      continue;
     }
+    for (int f = 0; f < F; f++) {
+      if (p.q_rank[Q * F + f] == 2) {
+        qc2[f]++;
+        qs2[f] += sz;
+      } else {
+        qc1[f]++;
+        qs1[f] += sz;
+      }
+    }
+  }
   int64_t two_blocks = 0;
   for (int64_t W = 0; W < p.n_fam; W++) {
     const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
@@ -526,14 +574,16 @@ mhc_status build_plan(Plan& p) {
       const int n = p.n_f[f], rho = p.fam_rank[W * F + f];
       if (n == 0) continue;
       fl += (double)p.n_snk * k * flops_member(n, rho);
+      fl += (double)one_sinks * flops_shared_rows(n, rho);
       if (rho == 1) {
-        fl += (double)two_q * flops_adjugate(n - 1) + (double)two_q_sinks * flops_kapply(n) +
-              (double)(p.n_snk - two_q_sinks) * flops_shared_rows(n, 1);
+        fl += (double)qc1[f] * flops_adjugate(n - 1) + (double)qs1[f] * flops_kapply(n);
+        fl += (double)qc2[f] * flops_block12(n) + (double)qs2[f] * flops_kapply12(n);
+        two_blocks += qc1[f] + qc2[f];
       } else {
-        fl += (double)two_q * flops_rank2_block(n) + (double)two_q_sinks * flops_kapply2(n) +
-              (double)(p.n_snk - two_q_sinks) * flops_shared_rows(n, rho);
+        fl += (double)qc1[f] * flops_rank2_block(n) + (double)qs1[f] * flops_kapply2(n);
+        fl += (double)qs2[f] * flops_shared_rows(n, rho);  // two changed rows and columns
+        two_blocks += qc1[f];
       }
-      two_blocks += two_q;
     }
   }
   p.two_sided_pairs = two_blocks;

@@ -43,7 +43,7 @@ void free_device(DevicePlan& d) {
   void* ptrs[] = {d.fam_info, d.fam_rank, d.fam_arow, d.mem_term, d.mem_par, d.mem_lab,
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
-                  d.snk_par2, d.snk_q, d.q_off, d.q_two, d.kbuf, d.kguard};
+                  d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& bi : d.bwd_index) {
@@ -130,6 +130,7 @@ mhc_status ensure_device(Plan& p) {
     if ((st = upload(&d.snk_q, p.snk_q.data(), p.snk_q.size())) != MHC_OK) return st;
     if ((st = upload(&d.q_off, p.q_off.data(), p.q_off.size())) != MHC_OK) return st;
     if ((st = upload(&d.q_two, p.q_two.data(), p.q_two.size())) != MHC_OK) return st;
+    if ((st = upload(&d.q_rank, p.q_rank.data(), p.q_rank.size())) != MHC_OK) return st;
     if ((st = upload<double>(&d.kbuf, nullptr, 2 * (size_t)p.n_fam * p.n_qfam * kstride)) != MHC_OK) return st;
     if ((st = upload<int32_t>(&d.kguard, nullptr, (size_t)p.n_fam * p.n_qfam * p.F)) != MHC_OK) return st;
     d.kstride = (int)kstride;
@@ -182,6 +183,7 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
     a.snk_par = p.dev.snk_par2;
     a.snk_q = p.dev.snk_q;
     a.q_two = p.dev.q_two;
+    a.q_rank = p.dev.q_rank;
     a.q_off = p.dev.q_off;
     a.kbuf = reinterpret_cast<const double2*>(p.dev.kbuf);
     a.kguard = p.dev.kguard;

@@ -63,6 +63,8 @@ def small_cases():
         "repeated_labels": rep,
         "diagonal_S": diag,
         "n32": wl.make_workload("n32", [32], [64], [3, 2], [40], seed=12),
+        "two_rows_both_sides": wl.make_workload("tworow", [12, 10], [60, 48], [9, 7, 5], [8, 6, 7, 5, 30],
+                                                seed=23, two_row_frac=0.5),
     }
 
 
