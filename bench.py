@@ -270,6 +270,8 @@ def run_gpu(args):
 
     if batched:
         batched["frac_of_fp64_peak"] = batched["tflops"] / (peak_flops / 1e12)
+    if adjoint:
+        adjoint["frac_of_fp64_peak"] = adjoint["tflops"] / (peak_flops / 1e12)
 
     line = None
     if rank == 0:
@@ -288,7 +290,7 @@ def run_gpu(args):
                          "flops_per_step": flops},
             "e2e": {"value": world * pairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 16},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (3 if st["two_sided_blocks"] > 0 else 2) * args.steps,
             "clocks": clocks,
             "refactors_per_step": refactor_pairs,
             "adjoint": adjoint,
@@ -325,9 +327,11 @@ def time_adjoint(mhc, plan, S, flush, stream, fwd_ms, pairs, steps=5):
         tot += e0.elapsed_time(e1)
     ms = tot / steps
     plan.status()
+    bflops = plan.stats()["backward_flops_per_call"]
     return {"ms_per_step": ms, "ratio_vs_forward": ms / fwd_ms, "pairs_per_s": pairs / (ms * 1e-3),
+            "tflops": bflops / (ms * 1e-3) / 1e12, "flops_per_step": bflops,
             "outputs": "dS_f (2 x 48 x 48 complex), dw_src [4096], dw_snk [4096]; L = Re C",
-            "gpu_launches_per_step": 5}
+            "gpu_launches_per_step": 6 if plan.stats()["two_sided_blocks"] > 0 else 5}
 
 
 def time_batch(mhc, flush, stream, count=64, reps=3):

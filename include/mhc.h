@@ -99,8 +99,9 @@ typedef struct {
   int64_t refactor_parent;       /* (member, sink, flavour) refactored by the pivot guard */
   int64_t refactor_child;        /* (member, sink, flavour) refactored by the lemma guard */
   int64_t sink_families;         /* sink-side families (two-sided update)             */
-  int64_t two_sided_blocks;      /* (family, sink family, flavour) blocks sharing adj(B) */
-  int64_t reserved[4];
+  int64_t two_sided_blocks;      /* (family, sink family, flavour) blocks sharing B's LU */
+  double backward_flops_per_call;/* algorithmic FP64 flops of one mhc_correlator_backward */
+  int64_t reserved[3];
 } mhc_stats;
 
 /* Thread-local message describing the last failure of this thread's last call. */

@@ -203,6 +203,14 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.dwsrc_part = reinterpret_cast<double2*>(d.bwd_wsrc);
   b.dwsnk_part = reinterpret_cast<double2*>(d.bwd_wsnk);
   const int nc = plan_ncmax(p);
+  if (b.a.snk_orig) {  // two-sided blocks: the factors of B first, as in the forward call
+    cudaError_t ek = nc <= 8 ? launch_kfac_nc8(b.a, p.n_fam, s)
+                             : (nc <= 18 ? launch_kfac_nc18(b.a, p.n_fam, s) : launch_kfac_nc32(b.a, p.n_fam, s));
+    if (ek != cudaSuccess) {
+      set_error(std::string("mhc_correlator_backward: launch: ") + cudaGetErrorString(ek));
+      return MHC_ECUDA;
+    }
+  }
   cudaError_t e = nc <= 8 ? launch_bwd_nc8(b, T, ctas, smem, s)
                           : (nc <= 18 ? launch_bwd_nc18(b, T, ctas, smem, s) : launch_bwd_nc32(b, T, ctas, smem, s));
   if (e != cudaSuccess) {

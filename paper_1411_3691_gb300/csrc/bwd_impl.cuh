@@ -231,6 +231,92 @@ __device__ __forceinline__ bool dispatch_lu_block(int n, const cd* S, int L, con
   }
 }
 
+// Scatter of one warp's 32 sinks into its accumulator rows (flavour f).  Lane s owns row
+// s: a shared row (s < n - 1, values from the staged cofactor block) or member s - n + 1
+// (gamma times the cached y).  Within a two-sided sink family the shared columns carry the
+// same labels for every sink, so their contributions are summed in registers and added to
+// the row once per family; the changed columns are added per sink.  Fixed order: no two
+// lanes touch the same row, and every lane walks the sinks and columns in order.
+template <int NC, int NFIX>
+__device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B, int f, int n_rt,
+                                             int kW, int mem0, int tile, int T, int warp, int lane,
+                                             const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 1;
+  const int nslots = M + kW;
+  for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
+    const bool act = s < nslots;
+    const int c = act && s >= M ? s - M : 0;
+    const int m = mem0 + c;
+    double wc = a.w_src[a.mem_term[m]];
+    if (__popc(a.mem_par[m]) & 1) wc = -wc;
+    cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
+    cd acc[NC];
+    int curQ = -2, nsh = 0;
+    const int32_t* curc = nullptr;
+    for (int jl = 0; jl <= 32; jl++) {
+      const int64_t jj = (int64_t)tile * T + warp * 32 + jl;
+      const bool live = jl < 32 && jj < a.n_snk;
+      const int Qj = live ? (a.snk_orig ? a.snk_q[jj] : -1) : -3;
+      if (Qj != curQ || Qj < 0) {  // flush the summed shared columns of the previous family
+        if (act) {
+#pragma unroll UNR
+          for (int q = 0; q < n; q++)
+            if (q < nsh) {
+              cd& d = Drow[curc[q]];
+              d.x += acc[q].x;
+              d.y += acc[q].y;
+            }
+        }
+        if (!live) break;
+        curQ = Qj;
+        curc = dev::sink_cols(a, jj) + a.off_f[f];
+        nsh = (Qj >= 0 && a.q_two[Qj]) ? n - a.q_rank[(int64_t)Qj * a.F + f] : 0;
+#pragma unroll UNR
+        for (int q = 0; q < n; q++) acc[q] = make_double2(0.0, 0.0);
+      }
+      const int ts = warp * 32 + jl;
+      cd g = make_double2(1.0, 0.0);
+      if (s >= M) {
+        const int64_t jo = a.snk_orig ? a.snk_orig[jj] : jj;
+        double w = wc * a.w_snk[jo];
+        if (a.snk_orig && (__popc(a.snk_par[jj]) & 1)) w = -w;
+        g = make_double2(w, 0.0);
+        for (int f2 = 0; f2 < a.F; f2++)
+          if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + ts]);
+      }
+      const int32_t* cj = dev::sink_cols(a, jj) + a.off_f[f];
+      const cd* st = Stage + (size_t)ts * B.mn_max + (s < M ? s * n : 0);
+#pragma unroll UNR
+      for (int q = 0; q < n; q++) {
+        const cd v = s < M ? st[q] : Ysm[(size_t)(a.yoff[f] + q) * T + ts];
+        if (q < nsh) {
+          acc[q] = dev::cfma(g, v, acc[q]);
+        } else if (act) {
+          cd& d = Drow[cj[q]];
+          d = dev::cfma(g, v, d);
+        }
+      }
+    }
+  }
+}
+
+template <int NCMAX>
+__device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs& B, int f, int n,
+                                                 int kW, int mem0, int tile, int T, int warp, int lane,
+                                                 const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
+  switch (n) {
+    case 1: scatter_rows<1, 1>(a, B, f, 1, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
+    case 2: scatter_rows<2, 2>(a, B, f, 2, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
+    case 3: scatter_rows<3, 3>(a, B, f, 3, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
+    case 4: scatter_rows<4, 4>(a, B, f, 4, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
+    case 5: scatter_rows<5, 5>(a, B, f, 5, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
+    case 6: scatter_rows<6, 6>(a, B, f, 6, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
+    default: scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df);
+  }
+}
+
 template <int NCMAX>
 __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
   const FwdArgs& a = B.a;
@@ -258,8 +344,13 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
   for (int tile = t0; tile < t1; tile++) {
     const int64_t jraw = (int64_t)tile * T + tid;
     const bool valid = jraw < a.n_snk;
-    const int64_t j = valid ? jraw : a.n_snk - 1;
-    const double wj = valid ? a.w_snk[j] : 0.0;
+    const int64_t j = valid ? jraw : a.n_snk - 1;  // sink position
+    const int32_t* cols = dev::sink_cols(a, j);
+    const int64_t jo = a.snk_orig ? a.snk_orig[j] : j;
+    const bool jpar = a.snk_orig && (__popc(a.snk_par[j]) & 1);
+    const double wj = valid ? (jpar ? -a.w_snk[jo] : a.w_snk[jo]) : 0.0;
+    const int Q = a.snk_orig ? a.snk_q[j] : -1;
+    const bool qtwo = Q >= 0 && a.q_two[Q];
 
     // ---- pass 1: cached solves, member dets (fresh where guarded), dw partials --------
     unsigned pguard = 0;
@@ -268,10 +359,21 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
       const int n = a.n_f[f];
       ey[f] = 0;
       if (n == 0) continue;
-      const bool g = dev::dispatch_shared<NCMAX>(
-          n, 1, a.S[f], a.L_f[f], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
-          a.snk_lab + j * a.Tn + a.off_f[f], Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f], a.kp);
-      pguard |= (unsigned)g << f;
+      const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+      if (qtwo && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+        // two-sided block: y from the stored factors of B (see kapply / kapply12)
+        const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
+        if (a.q_rank[(int64_t)Q * a.F + f] == 2)
+          dev::dispatch_kapply12<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+        else
+          dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                      Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+      } else {
+        const bool g = dev::dispatch_shared<NCMAX>(n, 1, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
+                                                   Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f], a.kp);
+        pguard |= (unsigned)g << f;
+      }
     }
     double2 accj = make_double2(0.0, 0.0);
     for (int c = 0; c < kW; c++) {
@@ -282,7 +384,7 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
         cd d = make_double2(1.0, 0.0);
         if (n > 0) {
           bool fail = (pguard >> f) & 1;
-          const int32_t* col = a.snk_lab + j * a.Tn + a.off_f[f];
+          const int32_t* col = cols + a.off_f[f];
           if (!fail)
             d = dev::dispatch_member<NCMAX>(n, 1, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
                                             col, Ysm + (size_t)a.yoff[f] * T + tid, T, ey[f], a.kc, &fail);
@@ -302,7 +404,8 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
       s.x = fma(wj, prod.x, s.x);
       s.y = fma(wj, prod.y, s.y);
     }
-    if (valid) B.dwsnk_part[(int64_t)W * a.n_snk + j] = accj;
+    if (jpar) accj = dev::cneg(accj);  // back to the sink's own column order
+    if (valid) B.dwsnk_part[(int64_t)W * a.n_snk + jo] = accj;
 
     // ---- pass 2 per flavour: h, shared-row cofactors, scatter -------------------------
     for (int f = 0; f < a.F; f++) {
@@ -311,7 +414,7 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
       const int M = n - 1;
       const cd* S = a.S[f];
       const int L = a.L_f[f];
-      const int32_t* col = a.snk_lab + j * a.Tn + a.off_f[f];
+      const int32_t* col = cols + a.off_f[f];
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
       cd h[NCMAX];
       for (int q = 0; q < n; q++) h[q] = make_double2(0.0, 0.0);
@@ -331,33 +434,8 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
       __syncwarp();
 
       // warp scatter: lane s owns accumulator row s (s < M: shared row; else member s - M)
-      cd* Df = Dw + (size_t)f * B.slots_max * B.Lmax;
-      const int nslots = M + kW;
-      for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
-        const bool act = s < nslots;
-        const int c = act && s >= M ? s - M : 0;
-        const int m = mem0 + c;
-        double wc = a.w_src[a.mem_term[m]];
-        if (__popc(a.mem_par[m]) & 1) wc = -wc;
-        cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
-        for (int jl = 0; jl < 32; jl++) {
-          const int64_t jj = (int64_t)tile * T + warp * 32 + jl;
-          if (jj >= a.n_snk) break;
-          const int ts = warp * 32 + jl;
-          cd g = make_double2(1.0, 0.0);
-          if (s >= M) {
-            g = make_double2(wc * a.w_snk[jj], 0.0);
-            for (int f2 = 0; f2 < a.F; f2++)
-              if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + ts]);
-          }
-          const int32_t* cj = a.snk_lab + jj * a.Tn + a.off_f[f];
-          const cd* st = Stage + (size_t)ts * B.mn_max + (s < M ? s * n : 0);
-          for (int q = 0; q < n; q++) {
-            const cd v = s < M ? st[q] : Ysm[(size_t)(a.yoff[f] + q) * T + ts];
-            if (act) Drow[cj[q]] = dev::cfma(g, v, Drow[cj[q]]);
-          }
-        }
-      }
+      dispatch_scatter<NCMAX>(a, B, f, n, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets,
+                              Dw + (size_t)f * B.slots_max * B.Lmax);
       __syncwarp();
     }
   }

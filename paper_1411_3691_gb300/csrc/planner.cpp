@@ -586,6 +586,25 @@ mhc_status build_plan(Plan& p) {
       }
     }
   }
+  // adjoint (rank-1 families only): the forward's solves and member dets again, then per
+  // (family, sink, flavour) the aggregated row h, the shared-row LU with the columns of
+  // A1^{-1} and the cofactor block, and per pair the scatter and the weight gradients
+  double bfl = fl;  // the forward part (without the final combine, added below)
+  for (int64_t W = 0; W < p.n_fam; W++) {
+    const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
+    for (int f = 0; f < F; f++) {
+      const int n = p.n_f[f];
+      if (n == 0) continue;
+      const double M = n - 1;
+      double blk = k * (6.0 * std::max(F - 1, 0) + 1.0 + 8.0 * n);  // gamma_c, h
+      blk += flops_shared_rows(n, 1) - 6.0 * M + 8.0 * n + 6.0;      // LU, z, h.z, alpha
+      for (int i = 0; i < (int)M; i++)                                 // columns of A1^{-1}
+        blk += 8.0 * (M - i - 1) * (M - i - 2) / 2.0 + 8.0 * M * (M - 1) / 2.0 + 6.0 * M;
+      blk += M * (8.0 * M + 6.0) + M * M * 14.0;                      // eta, beta, cofactor rows
+      blk += M * n * 2.0 + k * (n * 8.0 + 6.0 * std::max(F - 1, 0) + 1.0);  // scatter
+      bfl += (double)p.n_snk * blk;
+    }
+  }
   p.two_sided_pairs = two_blocks;
   s.two_sided_blocks = two_blocks;
   int Fa = 0;
@@ -593,6 +612,7 @@ mhc_status build_plan(Plan& p) {
   const double combine = 6.0 * std::max(Fa - 1, 0) + 1.0 + 4.0;  // flavour product, w_i w_j, accumulate
   fl += combine * (double)p.n_src * (double)p.n_snk;
   s.flops_per_call = fl;
+  s.backward_flops_per_call = bfl + (combine + 8.0) * (double)p.n_src * (double)p.n_snk;
   double fresh = 0.0;
   for (int f = 0; f < F; f++) fresh += flops_fresh_lu(p.n_f[f]);
   s.fresh_lu_flops_per_pair = fresh + combine;

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("fresh_lu_flops_per_pair", ctypes.c_double), ("bytes_per_call", ctypes.c_double),
                 ("plan_seconds", ctypes.c_double), ("refactor_parent", ctypes.c_int64),
                 ("refactor_child", ctypes.c_int64), ("sink_families", ctypes.c_int64),
-                ("two_sided_blocks", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
+                ("two_sided_blocks", ctypes.c_int64), ("backward_flops_per_call", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

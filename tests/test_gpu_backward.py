@@ -44,7 +44,7 @@ def gpu_backward(M, plan, S, g):
 def check_vs_oracle(M, w, opts=None):
     if opts is None:
         opts = M.default_opts()
-        opts.rank2 = 0
+        opts.rank2 = 0 if w.name != "tc" else 1
     plan = M.Plan.from_workload(w, opts)
     S = dev_S(w)
     ref = oracle.correlator_grad(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
@@ -78,7 +78,17 @@ CASES = {
     "n9_n12": lambda: wl.make_workload("n9n12", [9, 12], [36, 48], [5, 4], [20, 13], seed=10),
     "diagonal_S": lambda: _diag(),
     "repeated_labels": lambda: _repeat(),
+    "two_column_sink_families": lambda: _two_col_sinks(),
 }
+
+
+def _two_col_sinks():
+    """One-row source families against sink families that change two columns (n_f >= 10),
+    so the adjoint takes the two-column blocks of the two-sided update."""
+    a = wl.make_workload("tc", [12, 10], [60, 48], [7, 5, 4], [9, 6, 8, 5], seed=31, two_row_frac=0.0)
+    b = wl.make_workload("tc", [12, 10], [60, 48], [7, 5, 4], [9, 6, 8, 5], seed=31, two_row_frac=0.6)
+    assert all(np.array_equal(x, y) for x, y in zip(a.S, b.S))
+    return wl.Workload("tc", a.n_f, a.S, a.labels_src, a.w_src, b.labels_snk, b.w_snk)
 
 
 def _cut(w, n):
