@@ -12,6 +12,9 @@ namespace mhc {
 cudaError_t launch_bwd_nc8(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s);
 cudaError_t launch_bwd_nc18(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s);
 cudaError_t launch_bwd_nc32(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s);
+cudaError_t launch_kinv_nc8(const BwdArgs& b, int64_t n_fam, cudaStream_t s);
+cudaError_t launch_kinv_nc18(const BwdArgs& b, int64_t n_fam, cudaStream_t s);
+cudaError_t launch_kinv_nc32(const BwdArgs& b, int64_t n_fam, cudaStream_t s);
 int plan_ncmax(const Plan& p);
 mhc_status ensure_device(Plan& p);
 mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
@@ -203,9 +206,24 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.dwsrc_part = reinterpret_cast<double2*>(d.bwd_wsrc);
   b.dwsnk_part = reinterpret_cast<double2*>(d.bwd_wsnk);
   const int nc = plan_ncmax(p);
-  if (b.a.snk_orig) {  // two-sided blocks: the factors of B first, as in the forward call
+  b.kinv = nullptr;
+  if (b.a.snk_orig) {  // two-sided blocks: the factors of B, then B^{-1} for the cofactors
+    size_t kis = 0;
+    for (int f = 0; f < F; f++) {
+      b.kioff[f] = (int)kis;
+      kis += p.n_f[f] > 1 ? (size_t)(p.n_f[f] - 1) * (p.n_f[f] - 1) : 0;
+    }
+    b.kistride = (int)std::max<size_t>(kis, 1);
+    const size_t kcount = (size_t)p.n_fam * p.n_qfam * b.kistride;
+    if ((double)kcount * 16.0 <= 16e9) {
+      if ((st = dev_alloc(reinterpret_cast<double2**>(&d.kinv), kcount, &d.kinv_bytes)) != MHC_OK) return st;
+      b.kinv = reinterpret_cast<const double2*>(d.kinv);
+    }
     cudaError_t ek = nc <= 8 ? launch_kfac_nc8(b.a, p.n_fam, s)
                              : (nc <= 18 ? launch_kfac_nc18(b.a, p.n_fam, s) : launch_kfac_nc32(b.a, p.n_fam, s));
+    if (ek == cudaSuccess && b.kinv)
+      ek = nc <= 8 ? launch_kinv_nc8(b, p.n_fam, s)
+                   : (nc <= 18 ? launch_kinv_nc18(b, p.n_fam, s) : launch_kinv_nc32(b, p.n_fam, s));
     if (ek != cudaSuccess) {
       set_error(std::string("mhc_correlator_backward: launch: ") + cudaGetErrorString(ek));
       return MHC_ECUDA;

@@ -30,6 +30,9 @@ struct BwdArgs {
   double2* dS_part;     // [cta][warp][F][slots_max][Lmax]
   double2* dwsrc_part;  // [member][n_chunks]
   double2* dwsnk_part;  // [W][n_snk]
+  const double2* kinv;  // [W][Q][kistride]: B^{-1} row-major per flavour (two-sided blocks)
+  int kistride;
+  int kioff[MHC_FMAX];
 };
 
 namespace bwd {
@@ -231,6 +234,89 @@ __device__ __forceinline__ bool dispatch_lu_block(int n, const cd* S, int L, con
   }
 }
 
+// B^{-1} of every (one-row family, one-column sink family) block, from the LU factors the
+// forward stores (see kapply): column perm[i] of B^{-1} is U^{-1} L^{-1} e_i.  One thread
+// per block; blocks that are not two-sided, or whose pivot guard fired, are skipped.
+template <int NCMAX>
+__global__ void __launch_bounds__(128) kinv_kernel(const BwdArgs B, int64_t n_fam) {
+  const FwdArgs& a = B.a;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_fam * a.n_q * a.F) return;
+  const int f = (int)(t % a.F);
+  const int64_t wq = t / a.F;
+  const int Q = (int)(wq % a.n_q);
+  const int W = (int)(wq / a.n_q);
+  const int n = a.n_f[f];
+  if (n < 2 || !a.q_two[Q] || a.fam_rank[(int64_t)W * a.F + f] != 1 ||
+      a.q_rank[(int64_t)Q * a.F + f] != 1 || a.kguard[t])
+    return;
+  const int M = n - 1;
+  const cd* K = a.kbuf + wq * a.kstride + a.koff[f];
+  cd* X = const_cast<cd*>(B.kinv) + wq * B.kistride + B.kioff[f];
+  cd w[NCMAX];
+  for (int i = 0; i < M; i++) {
+    for (int p = 0; p < M; p++) {
+      if (p < i) {
+        w[p] = make_double2(0.0, 0.0);
+      } else if (p == i) {
+        w[p] = make_double2(1.0, 0.0);
+      } else {
+        cd s = dev::cneg(K[p * M + i]);
+        for (int q = i + 1; q < p; q++) s = dev::cfms(K[p * M + q], w[q], s);
+        w[p] = s;
+      }
+    }
+    for (int p = M - 1; p >= 0; p--) {
+      cd s = w[p];
+      for (int q = p + 1; q < M; q++) s = dev::cfms(K[p * M + q], w[q], s);
+      w[p] = dev::cmul(s, K[p * M + p]);
+    }
+    const int col = (int)K[M * M + i].x;
+    for (int u = 0; u < M; u++) X[u * M + col] = w[u];
+  }
+}
+
+// Shared-row cofactors of [A; h] for a two-sided block: with B^{-1} shared by the block,
+// y = det(B) [-B^{-1} a ; 1] the cached vector and eta = h[0..M) B^{-1},
+//   cof[m][q] = (h . y) B^{-1}[q][m] - eta_m y_q  (q < M),   cof[m][M] = -det(B) eta_m,
+// i.e. det(A1) [ (h . z)(u_m ; 0) - eta_m z ] with A1 = B; no division.
+template <int NC, int NFIX>
+__device__ __forceinline__ void two_cof(int n_rt, const cd* __restrict__ Binv, cd detB, const cd* h,
+                                        const cd* __restrict__ Y, int ys, cd* Mst) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 1;
+  cd y[NC];
+#pragma unroll UNR
+  for (int q = 0; q < n; q++) y[q] = Y[q * ys];
+  cd alpha = dev::cmul(h[0], y[0]);
+#pragma unroll UNR
+  for (int q = 1; q < n; q++) alpha = dev::cfma(h[q], y[q], alpha);
+#pragma unroll UNR
+  for (int m = 0; m < M; m++) {
+    cd eta = make_double2(0.0, 0.0);
+#pragma unroll UNR
+    for (int q = 0; q < M; q++) eta = dev::cfma(h[q], __ldg(Binv + q * M + m), eta);
+    cd* row = Mst + m * n;
+#pragma unroll UNR
+    for (int q = 0; q < M; q++) row[q] = dev::cfms(eta, y[q], dev::cmul(alpha, __ldg(Binv + q * M + m)));
+    row[M] = dev::cneg(dev::cmul(detB, eta));
+  }
+}
+
+template <int NCMAX>
+__device__ __forceinline__ void dispatch_two_cof(int n, const cd* Binv, cd detB, const cd* h,
+                                                 const cd* Y, int ys, cd* Mst) {
+  switch (n) {
+    case 2: two_cof<2, 2>(2, Binv, detB, h, Y, ys, Mst); return;
+    case 3: two_cof<3, 3>(3, Binv, detB, h, Y, ys, Mst); return;
+    case 4: two_cof<4, 4>(4, Binv, detB, h, Y, ys, Mst); return;
+    case 5: two_cof<5, 5>(5, Binv, detB, h, Y, ys, Mst); return;
+    case 6: two_cof<6, 6>(6, Binv, detB, h, Y, ys, Mst); return;
+    default: two_cof<NCMAX, 0>(n, Binv, detB, h, Y, ys, Mst);
+  }
+}
+
 // Scatter of one warp's 32 sinks into its accumulator rows (flavour f).  Lane s owns row
 // s: a shared row (s < n - 1, values from the staged cofactor block) or member s - n + 1
 // (gamma times the cached y).  Within a two-sided sink family the shared columns carry the
@@ -428,8 +514,20 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
         const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
         for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
       }
-      const bool ok = ((pguard >> f) & 1) ? false
-                                          : dispatch_lu_block<NCMAX>(n, S, L, arow, col, h, myStage, a.kp);
+      const int64_t blk = ((int64_t)W * a.n_q + Q) * a.F + f;
+      const bool twoc = B.kinv && qtwo && n >= 2 && a.q_rank[(int64_t)Q * a.F + f] == 1 && !a.kguard[blk];
+      bool ok;
+      if ((pguard >> f) & 1) {
+        ok = false;
+      } else if (twoc) {  // B^{-1} shared by the (family, sink family) block
+        const int64_t wq = (int64_t)W * a.n_q + Q;
+        const cd detB = a.kbuf[wq * a.kstride + a.koff[f] + M * M + M + 1];
+        dispatch_two_cof<NCMAX>(n, B.kinv + wq * B.kistride + B.kioff[f], detB, h,
+                                Ysm + (size_t)a.yoff[f] * T + tid, T, myStage);
+        ok = true;
+      } else {
+        ok = dispatch_lu_block<NCMAX>(n, S, L, arow, col, h, myStage, a.kp);
+      }
       if (!ok) minors_block<NCMAX>(S, L, n, arow, col, h, Ysm + (size_t)a.yoff[f] * T + tid, T, myStage);
       __syncwarp();
 
@@ -453,6 +551,14 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
 }
 
 }  // namespace bwd
+
+template <int NCMAX>
+cudaError_t launch_kinv_nc(const BwdArgs& b, int64_t n_fam, cudaStream_t s) {
+  const int64_t threads = n_fam * b.a.n_q * b.a.F;
+  if (threads == 0) return cudaSuccess;
+  bwd::kinv_kernel<NCMAX><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(b, n_fam);
+  return cudaGetLastError();
+}
 
 template <int NCMAX>
 cudaError_t launch_bwd_nc(const BwdArgs& b, int T, int64_t ctas, size_t smem, cudaStream_t s) {

@@ -8,4 +8,8 @@ cudaError_t launch_bwd_nc32(const BwdArgs& b, int T, int64_t ctas, size_t smem, 
   return launch_bwd_nc<32>(b, T, ctas, smem, s);
 }
 
+cudaError_t launch_kinv_nc32(const BwdArgs& b, int64_t n_fam, cudaStream_t s) {
+  return launch_kinv_nc<32>(b, n_fam, s);
+}
+
 }  // namespace mhc

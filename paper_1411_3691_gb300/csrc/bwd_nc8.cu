@@ -8,4 +8,8 @@ cudaError_t launch_bwd_nc8(const BwdArgs& b, int T, int64_t ctas, size_t smem, c
   return launch_bwd_nc<8>(b, T, ctas, smem, s);
 }
 
+cudaError_t launch_kinv_nc8(const BwdArgs& b, int64_t n_fam, cudaStream_t s) {
+  return launch_kinv_nc<8>(b, n_fam, s);
+}
+
 }  // namespace mhc
