@@ -126,11 +126,10 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   }
   ysl = std::max(ysl, 1);
   const int kmax = std::max(p.max_members, 1);
-  int T = 64;
-  auto smem_of = [&](int t) {
-    return ((size_t)(ysl + kmax * F + kmax) * t + (size_t)t * mn_max) * sizeof(double2);
-  };
-  if (smem_of(T) > 110 * 1024) T = 32;
+  // one warp per block: the per-sink state (cached solves, member determinants, weight
+  // accumulators) is all that lives in shared memory, so several warps fit per SM
+  const int T = 32;
+  auto smem_of = [&](int t) { return (size_t)(ysl + kmax * F + kmax) * t * sizeof(double2); };
   if (smem_of(T) > 220 * 1024) {
     set_error("mhc_correlator_backward: a family is too large for the adjoint's shared memory; "
               "plan with a smaller opts.max_family");
@@ -141,7 +140,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   const int n_tiles = (int)((p.n_snk + T - 1) / T);
   const int slots_max = Mmax + kmax;
   const size_t per_cta = (size_t)warps * F * slots_max * Lmax * sizeof(double2);
-  int n_chunks = (int)std::min<int64_t>(n_tiles, std::max<int64_t>(1, (16 * 152 + p.n_fam - 1) / p.n_fam));
+  int n_chunks = (int)std::min<int64_t>(n_tiles, std::max<int64_t>(1, (48 * 152 + p.n_fam - 1) / p.n_fam));
   while (n_chunks > 1 && (double)per_cta * p.n_fam * n_chunks > 1.0e9) n_chunks = (n_chunks + 1) / 2;
   const int tiles_per_cta = (n_tiles + n_chunks - 1) / n_chunks;
   n_chunks = (n_tiles + tiles_per_cta - 1) / tiles_per_cta;
@@ -156,6 +155,9 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
     return st;
   if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_wsnk), (size_t)p.n_fam * p.n_snk,
                       &d.bwd_wsnk_bytes)) != MHC_OK)
+    return st;
+  if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_stage), (size_t)ctas * T * mn_max,
+                      &d.bwd_stage_bytes)) != MHC_OK)
     return st;
   // row-label index of the accumulators, per flavour: label -> (family, slot) pairs
   if (d.bwd_index.empty()) {
@@ -205,6 +207,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.dS_part = reinterpret_cast<double2*>(d.bwd_rows);
   b.dwsrc_part = reinterpret_cast<double2*>(d.bwd_wsrc);
   b.dwsnk_part = reinterpret_cast<double2*>(d.bwd_wsnk);
+  b.stage = reinterpret_cast<double2*>(d.bwd_stage);
   const int nc = plan_ncmax(p);
   b.kinv = nullptr;
   if (b.a.snk_orig) {  // two-sided blocks: the factors of B, then B^{-1} for the cofactors

@@ -30,6 +30,7 @@ struct BwdArgs {
   double2* dS_part;     // [cta][warp][F][slots_max][Lmax]
   double2* dwsrc_part;  // [member][n_chunks]
   double2* dwsnk_part;  // [W][n_snk]
+  double2* stage;       // [cta][T][mn_max] shared-row cofactors of each sink, per block
   const double2* kinv;  // [W][Q][kistride]: B^{-1} row-major per flavour (two-sided blocks)
   int kistride;
   int kioff[MHC_FMAX];
@@ -404,7 +405,7 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
 }
 
 template <int NCMAX>
-__global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
+__global__ void __launch_bounds__(32) bwd_kernel(const BwdArgs B) {
   const FwdArgs& a = B.a;
   extern __shared__ double2 smem[];
   const int T = blockDim.x;
@@ -416,7 +417,8 @@ __global__ void __launch_bounds__(64) bwd_kernel(const BwdArgs B) {
   cd* Ysm = smem;
   cd* Dets = Ysm + (size_t)B.ysl * T;
   cd* AccS = Dets + (size_t)B.kmax * a.F * T;
-  cd* Stage = AccS + (size_t)B.kmax * T;
+  // staging of the shared-row cofactors: global scratch of this block (L1 resident)
+  cd* Stage = B.stage + (size_t)cta * T * B.mn_max;
   cd* myStage = Stage + (size_t)(warp * 32 + lane) * B.mn_max;
   cd* Dw = B.dS_part + ((size_t)(cta * B.warps + warp) * a.F) * B.slots_max * B.Lmax;
 
