@@ -59,9 +59,26 @@ def dist_env():
     return rank, world, local
 
 
-def workload(rank: int):
+def workload(rank: int, scale: float = 1.0):
+    """The rank's own replica: the He-4-like workload on its own propagators (seed)."""
     from paper_1411_3691_gb300 import workloads as wl
-    return wl.helium4(seed=1000 + 17 * rank)
+    return wl.helium4(scale=scale, seed=1000 + 17 * rank)
+
+
+def max_over_ranks(x: float, pg, device) -> float:
+    """The slowest rank's time: every rank gets the maximum (all-reduce MAX)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, pairs_per_rank: int, ms_per_step: float) -> float:
+    """Pairs per second of the whole job: every rank evaluates its own correlator of
+    pairs_per_rank pairs per step, the job's step lasting as long as its slowest rank."""
+    return world * pairs_per_rank / (ms_per_step * 1e-3)
 
 
 def cores():
@@ -223,13 +240,10 @@ def run_gpu(args):
     total_ms = sum(step_ms)
     plan.status()
     st = plan.stats()
-    if pg:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, pg, "cuda")
     pairs = len(w.w_src) * len(w.w_snk)
     ms_per_step = total_ms / args.steps
-    value = world * pairs / (ms_per_step * 1e-3)
+    value = whole_job_rate(world, pairs, ms_per_step)
 
     # roofline of the forward kernel (FP64 ALU bound): algorithmic flops per launch over the
     # step's device time, against the FP64 peak measured above
@@ -259,10 +273,7 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if pg:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, pg, "cuda")
     h2d = sum(h.numel() * h.element_size() for h in hS)
 
     adjoint = None if args.no_adjoint else time_adjoint(mhc, plan, S, flush, stream, ms_per_step, pairs)
@@ -288,7 +299,7 @@ def run_gpu(args):
                          "peak_source": "FP64 DFMA chains on all SMs, measured in this run "
                                         f"(nominal {NOMINAL_FP64_TFLOPS:.3f} from unit counts and clocks)",
                          "flops_per_step": flops},
-            "e2e": {"value": world * pairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": whole_job_rate(world, pairs, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 16},
             "gpu_launches": (3 if st["two_sided_blocks"] > 0 else 2) * args.steps,
             "clocks": clocks,
