@@ -221,20 +221,6 @@ __device__ __forceinline__ bool lu_block(const cd* __restrict__ S, int L, int n_
   return true;
 }
 
-template <int NCMAX>
-__device__ __forceinline__ bool dispatch_lu_block(int n, const cd* S, int L, const int32_t* arow,
-                                                  const int32_t* col, const cd* h, cd* Mst, int kp) {
-  switch (n) {
-    case 1: return lu_block<1, 1>(S, L, 1, arow, col, h, Mst, kp);
-    case 2: return lu_block<2, 2>(S, L, 2, arow, col, h, Mst, kp);
-    case 3: return lu_block<3, 3>(S, L, 3, arow, col, h, Mst, kp);
-    case 4: return lu_block<4, 4>(S, L, 4, arow, col, h, Mst, kp);
-    case 5: return lu_block<5, 5>(S, L, 5, arow, col, h, Mst, kp);
-    case 6: return lu_block<6, 6>(S, L, 6, arow, col, h, Mst, kp);
-    default: return lu_block<NCMAX, 0>(S, L, n, arow, col, h, Mst, kp);
-  }
-}
-
 // B^{-1} of every (one-row family, one-column sink family) block, from the LU factors the
 // forward stores (see kapply): column perm[i] of B^{-1} is U^{-1} L^{-1} e_i.  One thread
 // per block; blocks that are not two-sided, or whose pivot guard fired, are skipped.
@@ -305,17 +291,70 @@ __device__ __forceinline__ void two_cof(int n_rt, const cd* __restrict__ Binv, c
   }
 }
 
-template <int NCMAX>
-__device__ __forceinline__ void dispatch_two_cof(int n, const cd* Binv, cd detB, const cd* h,
-                                                 const cd* Y, int ys, cd* Mst) {
-  switch (n) {
-    case 2: two_cof<2, 2>(2, Binv, detB, h, Y, ys, Mst); return;
-    case 3: two_cof<3, 3>(3, Binv, detB, h, Y, ys, Mst); return;
-    case 4: two_cof<4, 4>(4, Binv, detB, h, Y, ys, Mst); return;
-    case 5: two_cof<5, 5>(5, Binv, detB, h, Y, ys, Mst); return;
-    case 6: two_cof<6, 6>(6, Binv, detB, h, Y, ys, Mst); return;
-    default: two_cof<NCMAX, 0>(n, Binv, detB, h, Y, ys, Mst);
+// Pass 2 of one (sink, flavour): the aggregated member row h = sum_c gamma_c g_c and the
+// shared-row cofactors of [A; h] into Mst (row-major M x n) -- from B^{-1} for a two-sided
+// block, from the recomputed shared-row LU otherwise, from signed minors where the pivot
+// guard fired.  With NFIX the row h stays in registers.
+template <int NC, int NFIX>
+__device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n_rt, int W,
+                                         int mem0, int kW, double wj, int tid, int T,
+                                         const int32_t* __restrict__ col, const int32_t* __restrict__ arow,
+                                         const cd* Dets, const cd* Y, bool guarded, const cd* Binv,
+                                         cd detB, cd* Mst) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const cd* S = a.S[f];
+  const int L = a.L_f[f];
+  cd h[NC];
+#pragma unroll UNR
+  for (int q = 0; q < n; q++) h[q] = make_double2(0.0, 0.0);
+  for (int c = 0; c < kW; c++) {
+    const int m = mem0 + c;
+    double wc = a.w_src[a.mem_term[m]] * wj;
+    if (__popc(a.mem_par[m]) & 1) wc = -wc;
+    cd g = make_double2(wc, 0.0);
+    for (int f2 = 0; f2 < a.F; f2++)
+      if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + tid]);
+    const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
   }
+  bool ok = false;
+  if (!guarded) {
+    if (Binv) {
+      two_cof<NC, NFIX>(n, Binv, detB, h, Y, T, Mst);
+      ok = true;
+    } else {
+      ok = lu_block<NC, NFIX>(S, L, n, arow, col, h, Mst, a.kp);
+    }
+  }
+  if (!ok) {
+    cd hl[NC];
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) hl[q] = h[q];
+    minors_block<NC>(S, L, n, arow, col, hl, const_cast<cd*>(Y), T, Mst);
+  }
+}
+
+template <int NCMAX>
+__device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n, int W,
+                                                  int mem0, int kW, double wj, int tid, int T,
+                                                  const int32_t* col, const int32_t* arow, const cd* Dets,
+                                                  const cd* Y, bool guarded, const cd* Binv, cd detB,
+                                                  cd* Mst) {
+#define MHC_COF(NN) cof_pass<NN, NN>(a, B, f, NN, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, \
+                                     Binv, detB, Mst)
+  switch (n) {
+    case 1: MHC_COF(1); return;
+    case 2: MHC_COF(2); return;
+    case 3: MHC_COF(3); return;
+    case 4: MHC_COF(4); return;
+    case 5: MHC_COF(5); return;
+    case 6: MHC_COF(6); return;
+    default:
+      cof_pass<NCMAX, 0>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, Binv, detB, Mst);
+  }
+#undef MHC_COF
 }
 
 // Scatter of one warp's 32 sinks into its accumulator rows (flavour f).  Lane s owns row
@@ -405,7 +444,7 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
 }
 
 template <int NCMAX>
-__global__ void __launch_bounds__(32) bwd_kernel(const BwdArgs B) {
+__global__ void __launch_bounds__(32, 1) bwd_kernel(const BwdArgs B) {
   const FwdArgs& a = B.a;
   extern __shared__ double2 smem[];
   const int T = blockDim.x;
@@ -500,37 +539,16 @@ __global__ void __launch_bounds__(32) bwd_kernel(const BwdArgs B) {
       const int n = a.n_f[f];
       if (n == 0) continue;
       const int M = n - 1;
-      const cd* S = a.S[f];
-      const int L = a.L_f[f];
       const int32_t* col = cols + a.off_f[f];
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
-      cd h[NCMAX];
-      for (int q = 0; q < n; q++) h[q] = make_double2(0.0, 0.0);
-      for (int c = 0; c < kW; c++) {
-        const int m = mem0 + c;
-        double wc = a.w_src[a.mem_term[m]] * wj;
-        if (__popc(a.mem_par[m]) & 1) wc = -wc;
-        cd g = make_double2(wc, 0.0);
-        for (int f2 = 0; f2 < a.F; f2++)
-          if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + tid]);
-        const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
-        for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
-      }
       const int64_t blk = ((int64_t)W * a.n_q + Q) * a.F + f;
       const bool twoc = B.kinv && qtwo && n >= 2 && a.q_rank[(int64_t)Q * a.F + f] == 1 && !a.kguard[blk];
-      bool ok;
-      if ((pguard >> f) & 1) {
-        ok = false;
-      } else if (twoc) {  // B^{-1} shared by the (family, sink family) block
-        const int64_t wq = (int64_t)W * a.n_q + Q;
-        const cd detB = a.kbuf[wq * a.kstride + a.koff[f] + M * M + M + 1];
-        dispatch_two_cof<NCMAX>(n, B.kinv + wq * B.kistride + B.kioff[f], detB, h,
-                                Ysm + (size_t)a.yoff[f] * T + tid, T, myStage);
-        ok = true;
-      } else {
-        ok = dispatch_lu_block<NCMAX>(n, S, L, arow, col, h, myStage, a.kp);
-      }
-      if (!ok) minors_block<NCMAX>(S, L, n, arow, col, h, Ysm + (size_t)a.yoff[f] * T + tid, T, myStage);
+      const int64_t wq = (int64_t)W * a.n_q + Q;
+      // B^{-1} shared by the (family, sink family) block
+      const cd* Binv = twoc ? B.kinv + wq * B.kistride + B.kioff[f] : nullptr;
+      const cd detB = twoc ? a.kbuf[wq * a.kstride + a.koff[f] + M * M + M + 1] : make_double2(0.0, 0.0);
+      dispatch_cof_pass<NCMAX>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets,
+                               Ysm + (size_t)a.yoff[f] * T + tid, (pguard >> f) & 1, Binv, detB, myStage);
       __syncwarp();
 
       // warp scatter: lane s owns accumulator row s (s < M: shared row; else member s - M)

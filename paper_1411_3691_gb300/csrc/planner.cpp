@@ -586,9 +586,11 @@ mhc_status build_plan(Plan& p) {
       }
     }
   }
-  // adjoint (rank-1 families only): the forward's solves and member dets again, then per
-  // (family, sink, flavour) the aggregated row h, the shared-row LU with the columns of
-  // A1^{-1} and the cofactor block, and per pair the scatter and the weight gradients
+  // adjoint (rank-1 families only): the forward's block factors, solves and member dets
+  // again; per (family, sink, flavour) the aggregated row h and the shared-row cofactor
+  // block -- from B^{-1} (computed once per two-sided block) for one-column sink families,
+  // from the recomputed shared-row LU with the columns of A1^{-1} otherwise; per pair the
+  // scatter and the weight gradients
   double bfl = fl;  // the forward part (without the final combine, added below)
   for (int64_t W = 0; W < p.n_fam; W++) {
     const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
@@ -596,13 +598,20 @@ mhc_status build_plan(Plan& p) {
       const int n = p.n_f[f];
       if (n == 0) continue;
       const double M = n - 1;
-      double blk = k * (6.0 * std::max(F - 1, 0) + 1.0 + 8.0 * n);  // gamma_c, h
-      blk += flops_shared_rows(n, 1) - 6.0 * M + 8.0 * n + 6.0;      // LU, z, h.z, alpha
-      for (int i = 0; i < (int)M; i++)                                 // columns of A1^{-1}
-        blk += 8.0 * (M - i - 1) * (M - i - 2) / 2.0 + 8.0 * M * (M - 1) / 2.0 + 6.0 * M;
-      blk += M * (8.0 * M + 6.0) + M * M * 14.0;                      // eta, beta, cofactor rows
-      blk += M * n * 2.0 + k * (n * 8.0 + 6.0 * std::max(F - 1, 0) + 1.0);  // scatter
-      bfl += (double)p.n_snk * blk;
+      const double gh = k * (6.0 * std::max(F - 1, 0) + 1.0 + 8.0 * n);       // gamma_c, h
+      double one = flops_shared_rows(n, 1) - 6.0 * M + 8.0 * n + 6.0;           // LU, z, h.z, alpha
+      double inv = 0.0;                                                         // columns of A1^{-1}
+      for (int i = 0; i < (int)M; i++)
+        inv += 8.0 * (M - i - 1) * (M - i - 2) / 2.0 + 8.0 * M * (M - 1) / 2.0 + 6.0 * M;
+      one += inv + M * (8.0 * M + 6.0) + M * M * 14.0;                          // eta, beta, cofactor rows
+      const double two = 8.0 * n - 2.0 + M * (22.0 * M + 6.0);                  // h.y, eta, cofactor rows
+      const double scat = M * n * 2.0 + k * (n * 8.0 + 6.0 * std::max(F - 1, 0) + 1.0);
+      bfl += (double)p.n_snk * (gh + scat);
+      if (p.fam_rank[W * F + f] == 1 && n >= 2) {
+        bfl += (double)(one_sinks + qs2[f]) * one + (double)qs1[f] * two + (double)qc1[f] * inv;
+      } else {
+        bfl += (double)p.n_snk * one;
+      }
     }
   }
   p.two_sided_pairs = two_blocks;

@@ -228,6 +228,24 @@ def test_flop_count_below_fresh_lu(M):
     assert 0 < per_pair < st["fresh_lu_flops_per_pair"] / 4
 
 
+def test_adjoint_flop_count_two_sided(M):
+    """The adjoint's count follows the path it takes: with sink families the shared-row
+    cofactors come from B^{-1} (one inverse per block) instead of a recomputed LU per
+    sink, so the two-sided count is lower than the one-sided one; both exceed the
+    forward, which the adjoint repeats."""
+    w = wl.helium4(scale=8 / 256)
+    two = M.Plan.from_workload(w).stats()
+    opts = M.default_opts()
+    opts.one_sided = 1
+    one = M.Plan.from_workload(w, opts).stats()
+    assert two["two_sided_blocks"] > 0 and one["two_sided_blocks"] == 0
+    assert two["backward_flops_per_call"] > two["flops_per_call"]
+    assert one["backward_flops_per_call"] > one["flops_per_call"]
+    d_fwd = one["flops_per_call"] - two["flops_per_call"]
+    d_bwd = one["backward_flops_per_call"] - two["backward_flops_per_call"]
+    assert d_bwd > d_fwd > 0
+
+
 @pytest.mark.parametrize("name", ["helium4", "mixed", "large"])
 def test_sink_families_two_sided(M, name):
     """Sink-side families: every position's aligned columns give the same determinant as
