@@ -22,27 +22,54 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
 
 namespace {
 
-// dS_f[a][b] = g conj(sum over (W, slot) rows labelled a, chunks, warps of the partials)
-__global__ void fin_dS_kernel(int f, int L, const int32_t* __restrict__ list_off,
-                              const int2* __restrict__ list, const double2* __restrict__ part,
-                              int n_chunks, int warps, int F, int slots_max, int Lmax,
-                              const double* __restrict__ g, double2* __restrict__ dS) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)L * L) return;
-  const int a = (int)(e / L), b = (int)(e % L);
+// dS_f[a][b] = g conj(sum over (W, slot) rows labelled a, chunks, warps of the partials).
+// One block per (row a, group of 32 columns): lane = column, the 8 warps take the terms
+// (row entry, chunk, warp) round-robin in a fixed order, then a fixed-order sum over the
+// warps -- the same result on every call.
+constexpr int kFinWarps = 8;
+__global__ void __launch_bounds__(32 * kFinWarps)
+    fin_dS_kernel(int f, int L, const int32_t* __restrict__ list_off, const int2* __restrict__ list,
+                  const double2* __restrict__ part, int n_chunks, int warps, int F, int slots_max,
+                  int Lmax, const double* __restrict__ g, double2* __restrict__ dS) {
+  __shared__ double2 red[kFinWarps][32];
+  const int a = blockIdx.y;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int b = blockIdx.x * 32 + lane;
+  const int bc = b < L ? b : L - 1;
+  const int k0 = list_off[a];
+  const int64_t per = (int64_t)n_chunks * warps;
+  const int nk = list_off[a + 1] - k0;
   double2 s = make_double2(0.0, 0.0);
-  for (int k = list_off[a]; k < list_off[a + 1]; k++) {
-    const int2 ws = list[k];
-    for (int c = 0; c < n_chunks; c++)
-      for (int w = 0; w < warps; w++) {
-        const int64_t cta = (int64_t)ws.x * n_chunks + c;
-        const double2 v = part[(((cta * warps + w) * F + f) * slots_max + ws.y) * Lmax + b];
-        s.x += v.x;
-        s.y += v.y;
-      }
+  // term t = k * per + cw (cw = chunk * warps + warp); this warp takes t = wp, wp + 8, ...
+  int k = 0;
+  int64_t cw = wp;
+  while (cw >= per) {
+    cw -= per;
+    k++;
   }
-  const double gr = g[0], gi = g[1];
-  dS[e] = make_double2(gr * s.x + gi * s.y, gi * s.x - gr * s.y);
+  while (k < nk) {
+    const int2 ws = list[k0 + k];
+    const int64_t row = (((int64_t)ws.x * per + cw) * F + f) * slots_max + ws.y;
+    const double2 v = part[row * Lmax + bc];
+    s.x += v.x;
+    s.y += v.y;
+    cw += kFinWarps;
+    while (cw >= per) {
+      cw -= per;
+      k++;
+    }
+  }
+  red[wp][lane] = s;
+  __syncthreads();
+  if (wp == 0 && b < L) {
+    double2 t = red[0][lane];
+    for (int w = 1; w < kFinWarps; w++) {
+      t.x += red[w][lane].x;
+      t.y += red[w][lane].y;
+    }
+    const double gr = g[0], gi = g[1];
+    dS[(int64_t)a * L + b] = make_double2(gr * t.x + gi * t.y, gi * t.x - gr * t.y);
+  }
 }
 
 // dw_src[i] = Re(conj(g) sum_chunks part[member(i)][chunk])
@@ -240,9 +267,8 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   }
   for (int f = 0; f < F; f++) {
     if (!dS_f || !dS_f[f]) continue;
-    const int L = p.L_f[f];
-    const int64_t cnt = (int64_t)L * L;
-    fin_dS_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+    const int L = p.L_f[f];  // 1 <= L <= 4096 (validated by the planner)
+    fin_dS_kernel<<<dim3((unsigned)((L + 31) / 32), (unsigned)L), 32 * kFinWarps, 0, s>>>(
         f, L, d.bwd_index[f].off, d.bwd_index[f].ent, b.dS_part, n_chunks, warps, F, slots_max,
         Lmax, g_out_dev, reinterpret_cast<double2*>(dS_f[f]));
   }
