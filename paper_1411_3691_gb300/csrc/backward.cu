@@ -156,7 +156,8 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   // one warp per block: the per-sink state (cached solves, member determinants, weight
   // accumulators) is all that lives in shared memory, so several warps fit per SM
   const int T = 32;
-  auto smem_of = [&](int t) { return (size_t)(ysl + kmax * F + kmax) * t * sizeof(double2); };
+  // cached solves [ysl][t] | member dets [F][kmax][t + 1] | dw_src accumulators [kmax][t]
+  auto smem_of = [&](int t) { return ((size_t)(ysl + kmax) * t + (size_t)kmax * F * (t + 1)) * sizeof(double2); };
   if (smem_of(T) > 220 * 1024) {
     set_error("mhc_correlator_backward: a family is too large for the adjoint's shared memory; "
               "plan with a smaller opts.max_family");

@@ -40,6 +40,13 @@ namespace bwd {
 
 using dev::cd;
 
+// Member determinants of the block's sinks in shared memory: [flavour][member][sink] with a
+// row pitch of T + 1, so that 8 consecutive members read by the scatter's lanes (one
+// 16-byte phase) fall in distinct bank groups.
+__device__ __forceinline__ size_t dix(int c, int f, int kmax, int T, int ts) {
+  return ((size_t)f * kmax + c) * (T + 1) + ts;
+}
+
 // det of an explicit n x n matrix in local memory (LU with partial pivoting; an exactly
 // zero pivot column gives 0).  B is destroyed.
 template <int NC>
@@ -227,10 +234,13 @@ __device__ __forceinline__ bool lu_block(const cd* __restrict__ S, int L, int n_
 template <int NCMAX>
 __global__ void __launch_bounds__(128) kinv_kernel(const BwdArgs B, int64_t n_fam) {
   const FwdArgs& a = B.a;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_fam * a.n_q * a.F) return;
-  const int f = (int)(t % a.F);
-  const int64_t wq = t / a.F;
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_fam * a.n_q * a.F) return;
+  // flavour slowest across threads (a warp shares n_f); t indexes the [W][Q][f] layout
+  const int64_t nwq = n_fam * a.n_q;
+  const int f = (int)(u / nwq);
+  const int64_t wq = u % nwq;
+  const int64_t t = wq * a.F + f;
   const int Q = (int)(wq % a.n_q);
   const int W = (int)(wq / a.n_q);
   const int n = a.n_f[f];
@@ -314,7 +324,7 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
     if (__popc(a.mem_par[m]) & 1) wc = -wc;
     cd g = make_double2(wc, 0.0);
     for (int f2 = 0; f2 < a.F; f2++)
-      if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + tid]);
+      if (f2 != f) g = dev::cmul(g, Dets[dix(c, f2, B.kmax, T, tid)]);
     const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
 #pragma unroll UNR
     for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
@@ -362,61 +372,78 @@ __device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArg
 // (gamma times the cached y).  Within a two-sided sink family the shared columns carry the
 // same labels for every sink, so their contributions are summed in registers and added to
 // the row once per family; the changed columns are added per sink.  Fixed order: no two
-// lanes touch the same row, and every lane walks the sinks and columns in order.
+// lanes touch the same row, and every lane walks the sinks and columns in order.  Each
+// sink's metadata (sink family, number of shared columns, column labels, weight) sits in
+// the registers of the sink's own lane and reaches the other lanes by shuffles.
 template <int NC, int NFIX>
 __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B, int f, int n_rt,
-                                             int kW, int mem0, int tile, int T, int warp, int lane,
-                                             const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
+                                             int kW, int mem0, int nlive, int T, int warp, int lane,
+                                             const int32_t* __restrict__ mycol, int myQ, int mynsh,
+                                             double mywj, const cd* Stage, const cd* Ysm,
+                                             const cd* Dets, cd* Df) {
   constexpr int UNR = NFIX ? NC : 1;
+  constexpr unsigned FULL = 0xffffffffu;
   const int n = NFIX ? NFIX : n_rt;
   const int M = n - 1;
   const int nslots = M + kW;
+  int cl[NC];
+#pragma unroll UNR
+  for (int q = 0; q < n; q++) cl[q] = mycol[q];
   for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
     const bool act = s < nslots;
-    const int c = act && s >= M ? s - M : 0;
+    const bool mem = s >= M;
+    const int c = act && mem ? s - M : 0;
     const int m = mem0 + c;
     double wc = a.w_src[a.mem_term[m]];
     if (__popc(a.mem_par[m]) & 1) wc = -wc;
     cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
     cd acc[NC];
+    int curlab[NC];
     int curQ = -2, nsh = 0;
-    const int32_t* curc = nullptr;
-    for (int jl = 0; jl <= 32; jl++) {
-      const int64_t jj = (int64_t)tile * T + warp * 32 + jl;
-      const bool live = jl < 32 && jj < a.n_snk;
-      const int Qj = live ? (a.snk_orig ? a.snk_q[jj] : -1) : -3;
-      if (Qj != curQ || Qj < 0) {  // flush the summed shared columns of the previous family
+#pragma unroll UNR
+    for (int q = 0; q < n; q++) {
+      acc[q] = make_double2(0.0, 0.0);
+      curlab[q] = 0;
+    }
+    for (int jl = 0; jl <= nlive; jl++) {
+      const bool live = jl < nlive;
+      const int src = jl & 31;
+      const int Qj = __shfl_sync(FULL, myQ, src);
+      const int nsj = __shfl_sync(FULL, mynsh, src);
+      const double wj = __shfl_sync(FULL, mywj, src);
+      int cj[NC];
+#pragma unroll UNR
+      for (int q = 0; q < n; q++) cj[q] = __shfl_sync(FULL, cl[q], src);
+      if (!live || Qj != curQ || Qj < 0) {  // flush the summed shared columns of the previous family
         if (act) {
 #pragma unroll UNR
           for (int q = 0; q < n; q++)
             if (q < nsh) {
-              cd& d = Drow[curc[q]];
+              cd& d = Drow[curlab[q]];
               d.x += acc[q].x;
               d.y += acc[q].y;
             }
         }
         if (!live) break;
         curQ = Qj;
-        curc = dev::sink_cols(a, jj) + a.off_f[f];
-        nsh = (Qj >= 0 && a.q_two[Qj]) ? n - a.q_rank[(int64_t)Qj * a.F + f] : 0;
+        nsh = nsj;
 #pragma unroll UNR
-        for (int q = 0; q < n; q++) acc[q] = make_double2(0.0, 0.0);
+        for (int q = 0; q < n; q++) {
+          acc[q] = make_double2(0.0, 0.0);
+          curlab[q] = cj[q];
+        }
       }
       const int ts = warp * 32 + jl;
       cd g = make_double2(1.0, 0.0);
-      if (s >= M) {
-        const int64_t jo = a.snk_orig ? a.snk_orig[jj] : jj;
-        double w = wc * a.w_snk[jo];
-        if (a.snk_orig && (__popc(a.snk_par[jj]) & 1)) w = -w;
-        g = make_double2(w, 0.0);
+      if (mem) {
+        g = make_double2(wc * wj, 0.0);
         for (int f2 = 0; f2 < a.F; f2++)
-          if (f2 != f) g = dev::cmul(g, Dets[((size_t)c * a.F + f2) * T + ts]);
+          if (f2 != f) g = dev::cmul(g, Dets[dix(c, f2, B.kmax, T, ts)]);
       }
-      const int32_t* cj = dev::sink_cols(a, jj) + a.off_f[f];
-      const cd* st = Stage + (size_t)ts * B.mn_max + (s < M ? s * n : 0);
+      const cd* st = Stage + (size_t)ts * B.mn_max + (mem ? 0 : s * n);
 #pragma unroll UNR
       for (int q = 0; q < n; q++) {
-        const cd v = s < M ? st[q] : Ysm[(size_t)(a.yoff[f] + q) * T + ts];
+        const cd v = mem ? Ysm[(size_t)(a.yoff[f] + q) * T + ts] : st[q];
         if (q < nsh) {
           acc[q] = dev::cfma(g, v, acc[q]);
         } else if (act) {
@@ -430,17 +457,23 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
 
 template <int NCMAX>
 __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs& B, int f, int n,
-                                                 int kW, int mem0, int tile, int T, int warp, int lane,
+                                                 int kW, int mem0, int nlive, int T, int warp, int lane,
+                                                 const int32_t* mycol, int myQ, int mynsh, double mywj,
                                                  const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
+#define MHC_SC(NN) scatter_rows<NN, NN>(a, B, f, NN, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, \
+                                        mywj, Stage, Ysm, Dets, Df)
   switch (n) {
-    case 1: scatter_rows<1, 1>(a, B, f, 1, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
-    case 2: scatter_rows<2, 2>(a, B, f, 2, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
-    case 3: scatter_rows<3, 3>(a, B, f, 3, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
-    case 4: scatter_rows<4, 4>(a, B, f, 4, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
-    case 5: scatter_rows<5, 5>(a, B, f, 5, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
-    case 6: scatter_rows<6, 6>(a, B, f, 6, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df); return;
-    default: scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets, Df);
+    case 1: MHC_SC(1); return;
+    case 2: MHC_SC(2); return;
+    case 3: MHC_SC(3); return;
+    case 4: MHC_SC(4); return;
+    case 5: MHC_SC(5); return;
+    case 6: MHC_SC(6); return;
+    default:
+      scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, mywj, Stage,
+                             Ysm, Dets, Df);
   }
+#undef MHC_SC
 }
 
 template <int NCMAX>
@@ -455,7 +488,7 @@ __global__ void __launch_bounds__(32, 1) bwd_kernel(const BwdArgs B) {
   // shared memory: y cache | dets [c][f] | dw_src accumulators [c] | staging [warp][lane][M n]
   cd* Ysm = smem;
   cd* Dets = Ysm + (size_t)B.ysl * T;
-  cd* AccS = Dets + (size_t)B.kmax * a.F * T;
+  cd* AccS = Dets + (size_t)B.kmax * a.F * (T + 1);
   // staging of the shared-row cofactors: global scratch of this block (L1 resident)
   cd* Stage = B.stage + (size_t)cta * T * B.mn_max;
   cd* myStage = Stage + (size_t)(warp * 32 + lane) * B.mn_max;
@@ -520,7 +553,7 @@ __global__ void __launch_bounds__(32, 1) bwd_kernel(const BwdArgs B) {
             d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, col);
           }
         }
-        Dets[((size_t)c * a.F + f) * T + tid] = d;
+        Dets[dix(c, f, B.kmax, T, tid)] = d;
         prod = f == 0 ? d : dev::cmul(prod, d);
       }
       double wc = a.w_src[a.mem_term[m]];
@@ -552,8 +585,11 @@ __global__ void __launch_bounds__(32, 1) bwd_kernel(const BwdArgs B) {
       __syncwarp();
 
       // warp scatter: lane s owns accumulator row s (s < M: shared row; else member s - M)
-      dispatch_scatter<NCMAX>(a, B, f, n, kW, mem0, tile, T, warp, lane, Stage, Ysm, Dets,
-                              Dw + (size_t)f * B.slots_max * B.Lmax);
+      const int mynsh = qtwo ? n - a.q_rank[(int64_t)Q * a.F + f] : 0;
+      const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
+      const int nlive = rem < 32 ? (int)rem : 32;
+      dispatch_scatter<NCMAX>(a, B, f, n, kW, mem0, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh,
+                              wj, Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax);
       __syncwarp();
     }
   }

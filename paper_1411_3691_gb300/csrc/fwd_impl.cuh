@@ -298,12 +298,21 @@ __device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_
   a.kguard[t] = g ? 1 : 0;
 }
 
+// Thread u of a plan's block grid takes flavour u / (n_fam n_q) and block u mod (n_fam n_q):
+// the flavour varies slowest, so a warp's threads share n_f (flavours of different sizes
+// would otherwise alternate across the lanes and run both code paths).  Returns the index
+// of the block in the [W][Q][f] layout of the factor buffer.
+__device__ __forceinline__ int64_t kfac_index(const FwdArgs& a, int64_t u, int64_t n_fam) {
+  const int64_t nwq = n_fam * a.n_q;
+  return (u % nwq) * a.F + u / nwq;
+}
+
 // two-sided blocks of one plan: one thread per (W, Q, f)
 template <int NCMAX>
 __global__ void __launch_bounds__(128) kfac_kernel(const FwdArgs a, int64_t n_fam) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_fam * a.n_q * a.F) return;
-  kfac_one<NCMAX>(a, t, n_fam);
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_fam * a.n_q * a.F) return;
+  kfac_one<NCMAX>(a, kfac_index(a, u, n_fam), n_fam);
 }
 
 // two-sided blocks of every plan of a batch in one launch: kpref[k] is the first thread of
@@ -321,7 +330,7 @@ __global__ void __launch_bounds__(128) kfac_batch_kernel(const FwdArgs* __restri
   }
   const FwdArgs& a = desc[lo];
   if (!a.snk_orig) return;
-  kfac_one<NCMAX>(a, t - kpref[lo], nfam[lo]);
+  kfac_one<NCMAX>(a, kfac_index(a, t - kpref[lo], nfam[lo]), nfam[lo]);
 }
 
 }  // namespace fwd
