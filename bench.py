@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward comparison")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="only measure the FP64 (DFMA) peak: >= 1 s of independent chains on every SM, "
+                         "SM clocks sampled meanwhile")
     return ap.parse_args()
 
 
@@ -392,8 +395,35 @@ def time_batch(mhc, flush, stream, count=64, reps=3):
             "graph": True}
 
 
+def run_fp64_peak(args):
+    """The roofline denominator on its own: DFMA chains on every SM for about 1.2 s, with the
+    SM clocks and throttle reasons sampled while it runs."""
+    import torch
+    from paper_1411_3691_gb300 import build as B
+    B.build()
+    from paper_1411_3691_gb300 import mhc
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    mhc.mhc_fp64_peak(20000)                    # warm-up
+    torch.cuda.synchronize()
+    iters = 1_250_000
+    t0 = time.perf_counter()
+    with Clocks(local) as clk:
+        flops = mhc.mhc_fp64_peak(iters)
+    secs = time.perf_counter() - t0
+    c = clk.summary()
+    nominal = NOMINAL_FP64_TFLOPS * (c["sm_mhz"] / 2070.0 if c.get("sm_mhz") else 1.0)
+    print(json.dumps({"metric": "FP64 DFMA peak", "value": flops / 1e12, "unit": "TFLOP/s",
+                      "seconds": secs, "dfma_per_s": flops / 2, "clocks": c,
+                      "nominal_at_median_clock": nominal,
+                      "kernel": "8 independent DFMA chains per thread, 2 x 256 threads per SM"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.fp64_peak:
+        run_fp64_peak(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

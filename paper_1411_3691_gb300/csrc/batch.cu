@@ -101,6 +101,7 @@ struct mhc_batch_s {
   int64_t* d_kpref = nullptr;     // [count + 1] first two-sided block thread of each plan
   int64_t* d_nfam = nullptr;      // [count] families per plan
   int64_t k_total = 0;
+  int k_big = 0;                  // a two-sided plan has a flavour with n > 6
   std::vector<const void*> key;  // S and out pointers the graph was captured with
   std::vector<double> tune_ms;   // measured time per candidate tile (32, 64, 128)
 };
@@ -192,11 +193,11 @@ cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
   // two-sided update: the factors of every (family, sink family) block of every
   // correlator, in one launch
   if (sh.ncmax <= 8)
-    e = launch_kfac_batch_nc8(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, s);
+    e = launch_kfac_batch_nc8(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
   else if (sh.ncmax <= 18)
-    e = launch_kfac_batch_nc18(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, s);
+    e = launch_kfac_batch_nc18(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
   else
-    e = launch_kfac_batch_nc32(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, s);
+    e = launch_kfac_batch_nc32(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
   if (e != cudaSuccess) return e;
   if (sh.ncmax <= 8)
     e = launch_batch_nc8(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
@@ -256,6 +257,7 @@ mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* p
     const Plan& p = *b->plans[k];
     nfam.push_back(p.n_fam);
     kpref.push_back(kpref.back() + (p.dev.two_sided ? p.n_fam * p.n_qfam * p.F : 0));
+    for (int f = 0; f < p.F; f++) b->k_big |= (p.dev.two_sided && p.n_f[f] > 6) ? 1 : 0;
   }
   b->k_total = kpref.back();
   if (cudaMalloc(&b->d_kpref, sizeof(int64_t) * (count + 1)) != cudaSuccess ||

@@ -540,6 +540,157 @@ __device__ __forceinline__ bool kfac_block12(const cd* __restrict__ S, int L, in
   return false;
 }
 
+// ------------------------------------------------------------------------------------
+// Group-cooperative factorisation of one two-sided block for n > 6.  A per-thread n x n
+// complex matrix no longer fits in registers there (17 x 17 at n = 18 is 4.6 KB), and in
+// local memory it streams from DRAM.  Instead G consecutive lanes share one block held in
+// shared memory: the rows below the pivot are dealt to the G lanes cyclically, so the
+// lanes of a warp stay busy with independent eliminations.  Group-local shuffles and
+// __syncwarp with the group's lane mask keep groups of one warp independent.
+// ------------------------------------------------------------------------------------
+
+// LU with partial pivoting of the R x C matrix B (shared memory, row pitch C), `steps`
+// pivot columns.  Pivot: the largest |re| + |im| in the column, ties to the lowest row.
+// Rows are exchanged whole (multipliers included); perm[i] = original row at position i.
+// On return B holds the multipliers below, U above and the reciprocal pivots on the
+// diagonal.  Returns true when the pivot guard fires (a zero pivot, or binary exponents of
+// the pivots more than kp apart).
+template <int G>
+__device__ __forceinline__ bool group_lu(cd* B, int* perm, int R, int C, int steps, int g, unsigned gm,
+                                         int kp, cd* det_out, int* par_out) {
+  for (int i = g; i < R; i += G) perm[i] = i;
+  __syncwarp(gm);
+  int parity = 0, emin = 4096, emax = -4096;
+  bool zero = false;
+  cd det = make_double2(1.0, 0.0);
+  for (int k = 0; k < steps; k++) {
+    double best = 0.0;
+    int idx = -1;
+    for (int i = k + g; i < R; i += G) {
+      const double m = abs1(B[i * C + k]);
+      if (idx < 0 || gt_nonneg(m, best)) {
+        best = m;
+        idx = i;
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) {
+      const double ob = __shfl_xor_sync(gm, best, off);
+      const int oi = __shfl_xor_sync(gm, idx, off);
+      const bool take = oi >= 0 && (idx < 0 || gt_nonneg(ob, best) || (!gt_nonneg(best, ob) && oi < idx));
+      best = take ? ob : best;
+      idx = take ? oi : idx;
+    }
+    const int p = idx;
+    if (p != k) {
+      for (int u = g; u < C; u += G) {
+        const cd t = B[k * C + u];
+        B[k * C + u] = B[p * C + u];
+        B[p * C + u] = t;
+      }
+      if (g == 0) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+      parity ^= 1;
+    }
+    __syncwarp(gm);
+    const cd piv = B[k * C + k];
+    const int e = expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    det = (k == 0) ? piv : cmul(det, piv);
+    const cd rc = crcp(piv);
+    for (int i = k + 1 + g; i < R; i += G) {
+      const cd l = cmul(B[i * C + k], rc);
+      B[i * C + k] = l;
+      for (int u = k + 1; u < C; u++) B[i * C + u] = cfms(l, B[k * C + u], B[i * C + u]);
+    }
+    __syncwarp(gm);
+    if (g == 0) B[k * C + k] = rc;
+  }
+  __syncwarp(gm);
+  *det_out = det;
+  *par_out = parity;
+  return steps > 0 && (zero || emax - emin > kp);
+}
+
+// Group version of kfac_block (RHO = 1, 2) for the n > 6 blocks; same factor layout.
+// Bs: (NC-1)^2 complex scratch, Ws: NC-1 complex, Ps: NC-1 ints, all in shared memory.
+template <int G>
+__device__ __forceinline__ bool group_kfac_block(const cd* __restrict__ S, int L, int n, int rho,
+                                                 const int32_t* __restrict__ arow,
+                                                 const int32_t* __restrict__ scol, cd* __restrict__ K,
+                                                 int kp, int g, unsigned gm, cd* Bs, cd* Ws, int* Ps) {
+  const int M = n - rho;
+  const int C = rho == 2 ? M + 1 : M;
+  for (int e = g; e < M * C; e += G) {
+    const int i = e / C, u = e - i * C;
+    Bs[e] = ldS(S + (size_t)arow[i] * L + scol[u]);
+  }
+  __syncwarp(gm);
+  cd det;
+  int parity;
+  if (group_lu<G>(Bs, Ps, M, C, M, g, gm, kp, &det, &parity)) return true;
+  const cd sd = parity ? cneg(det) : det;
+  if (rho == 2) {  // w = -U1^{-1} u, u the transformed extra column
+    for (int p = M - 1; p >= 0; p--) {
+      cd s = make_double2(0.0, 0.0);
+      for (int q = p + 1 + g; q < M; q += G) s = cfma(Bs[p * C + q], Ws[q], s);
+#pragma unroll
+      for (int off = 1; off < G; off <<= 1) {
+        s.x += __shfl_xor_sync(gm, s.x, off);
+        s.y += __shfl_xor_sync(gm, s.y, off);
+      }
+      if (g == 0) {
+        const cd b = Bs[p * C + M];
+        Ws[p] = cmul(make_double2(b.x + s.x, b.y + s.y), cneg(Bs[p * C + p]));
+      }
+      __syncwarp(gm);
+    }
+  }
+  for (int e = g; e < M * M; e += G) {
+    const int i = e / M, u = e - i * M;
+    K[e] = Bs[i * C + u];
+  }
+  for (int i = g; i < M; i += G) K[M * M + i] = make_double2((double)Ps[i], 0.0);
+  if (rho == 1) {
+    if (g == 0) {
+      K[M * M + M] = cneg(sd);
+      K[M * M + M + 1] = sd;
+    }
+  } else {
+    for (int i = g; i < M; i += G) K[M * M + M + i] = Ws[i];
+    if (g == 0) K[M * M + 2 * M] = sd;
+  }
+  __syncwarp(gm);
+  return false;
+}
+
+// Group version of kfac_block12 for the n > 6 blocks; same factor layout.
+template <int G>
+__device__ __forceinline__ bool group_kfac_block12(const cd* __restrict__ S, int L, int n,
+                                                   const int32_t* __restrict__ arow,
+                                                   const int32_t* __restrict__ scol, cd* __restrict__ K,
+                                                   int kp, int g, unsigned gm, cd* Bs, int* Ps) {
+  const int M = n - 1, C = n - 2;
+  for (int e = g; e < M * C; e += G) {
+    const int i = e / C, u = e - i * C;
+    Bs[e] = ldS(S + (size_t)arow[i] * L + scol[u]);
+  }
+  __syncwarp(gm);
+  cd det;
+  int parity;
+  if (group_lu<G>(Bs, Ps, M, C, C, g, gm, kp, &det, &parity)) return true;
+  for (int e = g; e < M * C; e += G) K[e] = Bs[e];
+  for (int i = g; i < M; i += G) K[M * C + i] = make_double2((double)Ps[i], 0.0);
+  if (g == 0) K[M * C + M] = parity ? cneg(det) : det;
+  __syncwarp(gm);
+  return false;
+}
+
 // Fresh determinant of one n x n block by LU with partial pivoting (the refactor path):
 // rows S[rows[m]], columns col[q].
 template <int NC, int NFIX>

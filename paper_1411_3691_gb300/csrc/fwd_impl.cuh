@@ -247,7 +247,7 @@ __device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_
   const int Q = (int)(wq % a.n_q);
   const int W = (int)(wq / a.n_q);
   const int n = a.n_f[f];
-  if (n == 0 || !a.q_two[Q]) return;
+  if (n == 0 || n > 6 || !a.q_two[Q]) return;  // n > 6: kfac_group_kernel
   const int rho = a.fam_rank[(int64_t)W * a.F + f];
   const int sig = a.q_rank[(int64_t)Q * a.F + f];
   const dev::cd* S = a.S[f];
@@ -272,7 +272,7 @@ __device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_
       MHC_K12(5)
       MHC_K12(6)
       default:
-        g = dev::kfac_block12<NCMAX, 0>(S, L, n, arow, scol, K, a.kp);
+        return;
     }
 #undef MHC_K12
     a.kguard[t] = g ? 1 : 0;
@@ -291,8 +291,7 @@ __device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_
     MHC_KF(5)
     MHC_KF(6)
     default:
-      g = rho == 1 ? dev::kfac_block<NCMAX, 0, 1>(S, L, n, arow, scol, K, a.kp)
-                   : dev::kfac_block<NCMAX, 0, 2>(S, L, n, arow, scol, K, a.kp);
+      return;
   }
 #undef MHC_KF
   a.kguard[t] = g ? 1 : 0;
@@ -333,13 +332,87 @@ __global__ void __launch_bounds__(128) kfac_batch_kernel(const FwdArgs* __restri
   kfac_one<NCMAX>(a, kfac_index(a, t - kpref[lo], nfam[lo]), nfam[lo]);
 }
 
-}  // namespace fwd
+// Two-sided blocks with n > 6: G lanes per block, the block in shared memory (see
+// dev::group_lu).  One warp per thread block; GPW blocks per warp.
+template <int NCMAX>
+struct KGroup {
+  static constexpr int G = NCMAX <= 18 ? 4 : 16;              // lanes per block
+  static constexpr int GPW = 32 / G;                           // blocks per warp
+  static constexpr int BS = (NCMAX - 1) * (NCMAX - 1) + (NCMAX - 1);  // complex per block
+  static constexpr int PS = NCMAX;                             // ints per block
+  static constexpr size_t smem() { return (size_t)GPW * (BS * sizeof(double2) + PS * sizeof(int)); }
+};
 
 template <int NCMAX>
+__device__ __forceinline__ void kfac_group_one(const FwdArgs& a, int64_t t) {
+  using KG = KGroup<NCMAX>;
+  extern __shared__ double2 ksm[];
+  const int lane = threadIdx.x & 31;
+  const int j = lane / KG::G, g = lane % KG::G;
+  const unsigned gm = KG::G == 32 ? 0xffffffffu : (((1u << KG::G) - 1u) << (j * KG::G));
+  dev::cd* Bs = ksm + (size_t)j * KG::BS;
+  dev::cd* Ws = Bs + (NCMAX - 1) * (NCMAX - 1);
+  int* Ps = reinterpret_cast<int*>(ksm + (size_t)KG::GPW * KG::BS) + j * KG::PS;
+  const int f = (int)(t % a.F);
+  const int64_t wq = t / a.F;
+  const int Q = (int)(wq % a.n_q);
+  const int W = (int)(wq / a.n_q);
+  const int n = a.n_f[f];
+  if (n <= 6 || !a.q_two[Q]) return;
+  const int rho = a.fam_rank[(int64_t)W * a.F + f];
+  const int sig = a.q_rank[(int64_t)Q * a.F + f];
+  const dev::cd* S = a.S[f];
+  const int L = a.L_f[f];
+  const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+  const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
+  dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
+  bool gd;
+  if (rho == 2 && sig == 2)  // two changed rows and columns: one-sided update
+    gd = true;
+  else if (sig == 2)
+    gd = dev::group_kfac_block12<KG::G>(S, L, n, arow, scol, K, a.kp, g, gm, Bs, Ps);
+  else
+    gd = dev::group_kfac_block<KG::G>(S, L, n, rho, arow, scol, K, a.kp, g, gm, Bs, Ws, Ps);
+  if (g == 0) a.kguard[t] = gd ? 1 : 0;
+}
+
+template <int NCMAX>
+__global__ void __launch_bounds__(32) kfac_group_kernel(const FwdArgs a, int64_t n_fam) {
+  const int64_t u = (int64_t)blockIdx.x * KGroup<NCMAX>::GPW + (threadIdx.x / KGroup<NCMAX>::G);
+  if (u >= n_fam * a.n_q * a.F) return;
+  kfac_group_one<NCMAX>(a, kfac_index(a, u, n_fam));
+}
+
+template <int NCMAX>
+__global__ void __launch_bounds__(32) kfac_group_batch_kernel(const FwdArgs* __restrict__ desc,
+                                                              const int64_t* __restrict__ kpref,
+                                                              const int64_t* __restrict__ nfam, int count) {
+  const int64_t t = (int64_t)blockIdx.x * KGroup<NCMAX>::GPW + (threadIdx.x / KGroup<NCMAX>::G);
+  if (t >= kpref[count]) return;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {  // last k with kpref[k] <= t
+    const int mid = (lo + hi + 1) >> 1;
+    if (kpref[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const FwdArgs& a = desc[lo];
+  if (!a.snk_orig) return;
+  kfac_group_one<NCMAX>(a, kfac_index(a, t - kpref[lo], nfam[lo]));
+}
+
+}  // namespace fwd
+
+// Block factors of every plan of a batch: blocks with n <= 6 one per thread, blocks with
+// n > 6 (present when big != 0) by lane groups.
+template <int NCMAX>
 cudaError_t launch_kfac_batch_nc(const FwdArgs* desc, const int64_t* kpref, const int64_t* nfam,
-                                 int count, int64_t total, cudaStream_t s) {
+                                 int count, int64_t total, int big, cudaStream_t s) {
   if (total == 0) return cudaSuccess;
   fwd::kfac_batch_kernel<NCMAX><<<(unsigned)((total + 127) / 128), 128, 0, s>>>(desc, kpref, nfam, count);
+  if (big) {
+    using KG = fwd::KGroup<NCMAX>;
+    fwd::kfac_group_batch_kernel<NCMAX><<<(unsigned)((total + KG::GPW - 1) / KG::GPW), 32, KG::smem(), s>>>(
+        desc, kpref, nfam, count);
+  }
   return cudaGetLastError();
 }
 
@@ -348,6 +421,12 @@ cudaError_t launch_kfac_nc(const FwdArgs& a, int64_t n_fam, cudaStream_t s) {
   const int64_t threads = n_fam * a.n_q * a.F;
   if (threads == 0) return cudaSuccess;
   fwd::kfac_kernel<NCMAX><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a, n_fam);
+  bool big = false;
+  for (int f = 0; f < a.F; f++) big |= a.n_f[f] > 6;
+  if (big) {
+    using KG = fwd::KGroup<NCMAX>;
+    fwd::kfac_group_kernel<NCMAX><<<(unsigned)((threads + KG::GPW - 1) / KG::GPW), 32, KG::smem(), s>>>(a, n_fam);
+  }
   return cudaGetLastError();
 }
 

@@ -23,8 +23,8 @@ cudaError_t launch_batch_nc32(int grid, int T, size_t smem, cudaStream_t s, cons
 int batch_occupancy_nc32(int T, size_t smem) { return batch_occupancy_nc<32>(T, smem); }
 
 cudaError_t launch_kfac_batch_nc32(const FwdArgs* desc, const int64_t* kpref, const int64_t* nfam,
-                                  int count, int64_t total, cudaStream_t s) {
-  return launch_kfac_batch_nc<32>(desc, kpref, nfam, count, total, s);
+                                  int count, int64_t total, int big, cudaStream_t s) {
+  return launch_kfac_batch_nc<32>(desc, kpref, nfam, count, total, big, s);
 }
 
 cudaError_t launch_kfac_nc32(const FwdArgs& a, int64_t n_fam, cudaStream_t s) {

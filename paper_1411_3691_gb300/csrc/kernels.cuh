@@ -254,7 +254,7 @@ size_t forward_smem_bytes(int slots, int tile);
   cudaError_t launch_kfac_nc##NC(const FwdArgs& a, int64_t n_fam, cudaStream_t s);           \
   cudaError_t launch_kfac_batch_nc##NC(const FwdArgs* desc, const int64_t* kpref,            \
                                        const int64_t* nfam, int count, int64_t total,         \
-                                       cudaStream_t s);
+                                       int big, cudaStream_t s);
 MHC_DECL_NC(8)
 MHC_DECL_NC(18)
 MHC_DECL_NC(32)
