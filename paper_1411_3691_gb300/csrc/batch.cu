@@ -70,14 +70,22 @@ __global__ void scratch_S(double2* S, int L, uint32_t seed) {
 
 }  // namespace
 
+// The correlators of a batch by n class (largest n_f of the plan <= 8, 18, 32): each class
+// has its own item queue and its own persistent kernel, compiled for that class, so the
+// small-n correlators keep the register budget (and occupancy) of their class.
+constexpr int kClasses = 3;
+constexpr int kClassNc[kClasses] = {8, 18, 32};
+
 // One launch configuration of a batch (a sink tile T).
 struct BatchShape {
-  int T = 0, grid = 0, ncmax = 8;
-  size_t smem = 0;
+  int T = 0, ncmax = 8;
   int64_t n_items = 0;
-  std::vector<BatchItem> items;
+  std::vector<BatchItem> items;   // class by class, each in decreasing cost
   std::vector<int64_t> part_off;  // [count + 1]
   std::vector<int> n_tiles;       // per correlator
+  int64_t cls_off[kClasses + 1] = {0, 0, 0, 0};  // items of class c: [cls_off[c], cls_off[c + 1])
+  int cls_grid[kClasses] = {0, 0, 0};
+  size_t cls_smem[kClasses] = {0, 0, 0};
 };
 
 }  // namespace mhc
@@ -102,11 +110,18 @@ struct mhc_batch_s {
   int64_t* d_nfam = nullptr;      // [count] families per plan
   int64_t k_total = 0;
   int k_big = 0;                  // a two-sided plan has a flavour with n > 6
+  cudaStream_t side = nullptr;    // second branch: the class kernels run concurrently
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<const void*> key;  // S and out pointers the graph was captured with
   std::vector<double> tune_ms;   // measured time per candidate tile (32, 64, 128)
 };
 
 namespace {
+
+int class_of(const Plan& p) {
+  const int nc = plan_ncmax(p);
+  return nc <= 8 ? 0 : (nc <= 18 ? 1 : 2);
+}
 
 BatchShape make_shape(const mhc_batch_s& b, int T) {
   BatchShape sh;
@@ -115,17 +130,18 @@ BatchShape make_shape(const mhc_batch_s& b, int T) {
     double c;
     BatchItem it;
   };
-  std::vector<Cost> all;
+  std::vector<Cost> all[kClasses];
   sh.part_off.push_back(0);
-  int max_slots = 1;
+  int max_slots[kClasses] = {1, 1, 1};
   for (int k = 0; k < b.count; k++) {
     const Plan& p = *b.plans[k];
     const int nt = (int)((p.n_snk + T - 1) / T);
+    const int cl = class_of(p);
     sh.n_tiles.push_back(nt);
     sh.ncmax = std::max(sh.ncmax, plan_ncmax(p));
     int yoff[MHC_FMAX], slots = 0;
     plan_slots(p, yoff, &slots);
-    max_slots = std::max(max_slots, slots);
+    max_slots[cl] = std::max(max_slots[cl], slots);
     for (int64_t W = 0; W < p.n_fam; W++) {
       double c = 0.0;
       const double kW = (double)(p.fam_off[W + 1] - p.fam_off[W]);
@@ -135,26 +151,34 @@ BatchShape make_shape(const mhc_batch_s& b, int T) {
       }
       for (int t = 0; t < nt; t++) {
         const double width = (double)std::min<int64_t>(T, p.n_snk - (int64_t)t * T);
-        all.push_back({c * width, BatchItem{k, (int32_t)W, t, 0}});
+        all[cl].push_back({c * width, BatchItem{k, (int32_t)W, t, 0}});
       }
     }
     sh.part_off.push_back(sh.part_off.back() + p.n_fam * nt);
   }
-  std::stable_sort(all.begin(), all.end(), [](const Cost& x, const Cost& y) { return x.c > y.c; });
-  for (auto& c : all) sh.items.push_back(c.it);
-  sh.n_items = (int64_t)sh.items.size();
-  sh.smem = forward_smem_bytes(max_slots, T);
-  int occ = 1;
-  if (sh.ncmax <= 8)
-    occ = batch_occupancy_nc8(T, sh.smem);
-  else if (sh.ncmax <= 18)
-    occ = batch_occupancy_nc18(T, sh.smem);
-  else
-    occ = batch_occupancy_nc32(T, sh.smem);
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device);
-  sh.grid = (int)std::min<int64_t>((int64_t)sms * occ, std::max<int64_t>(sh.n_items, 1));
+  for (int c = 0; c < kClasses; c++) {
+    std::stable_sort(all[c].begin(), all[c].end(), [](const Cost& x, const Cost& y) { return x.c > y.c; });
+    sh.cls_off[c] = (int64_t)sh.items.size();
+    for (auto& x : all[c]) sh.items.push_back(x.it);
+    const int64_t n = (int64_t)all[c].size();
+    if (n == 0) continue;
+    sh.cls_smem[c] = forward_smem_bytes(max_slots[c], T);
+    const int occ = c == 0 ? batch_occupancy_nc8(T, sh.cls_smem[c])
+                           : (c == 1 ? batch_occupancy_nc18(T, sh.cls_smem[c])
+                                     : batch_occupancy_nc32(T, sh.cls_smem[c]));
+    sh.cls_grid[c] = (int)std::min<int64_t>((int64_t)sms * occ, n);
+  }
+  sh.cls_off[kClasses] = (int64_t)sh.items.size();
+  sh.n_items = (int64_t)sh.items.size();
   return sh;
+}
+
+size_t max_smem(const BatchShape& sh) {
+  size_t m = 0;
+  for (int c = 0; c < kClasses; c++) m = std::max(m, sh.cls_smem[c]);
+  return m;
 }
 
 mhc_status fill_descs(mhc_batch_s& b, const BatchShape& sh, const double* const* const* S,
@@ -187,11 +211,25 @@ mhc_status upload_shape(mhc_batch_s& b, const BatchShape& sh) {
   return MHC_OK;
 }
 
+cudaError_t launch_class(const mhc_batch_s& b, const BatchShape& sh, int c, cudaStream_t s) {
+  const BatchItem* items = b.d_items + sh.cls_off[c];
+  const int64_t n = sh.cls_off[c + 1] - sh.cls_off[c];
+  unsigned long long* head = b.d_head + c;
+  if (c == 0)
+    return launch_batch_nc8(sh.cls_grid[c], sh.T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
+                            b.d_partials);
+  if (c == 1)
+    return launch_batch_nc18(sh.cls_grid[c], sh.T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
+                             b.d_partials);
+  return launch_batch_nc32(sh.cls_grid[c], sh.T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
+                           b.d_partials);
+}
+
 cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b.d_head, 0, sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(b.d_head, 0, sizeof(unsigned long long) * kClasses, s);
   if (e != cudaSuccess) return e;
   // two-sided update: the factors of every (family, sink family) block of every
-  // correlator, in one launch
+  // correlator, in one launch (two when some flavour has n > 6)
   if (sh.ncmax <= 8)
     e = launch_kfac_batch_nc8(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
   else if (sh.ncmax <= 18)
@@ -199,13 +237,32 @@ cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
   else
     e = launch_kfac_batch_nc32(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
   if (e != cudaSuccess) return e;
-  if (sh.ncmax <= 8)
-    e = launch_batch_nc8(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
-  else if (sh.ncmax <= 18)
-    e = launch_batch_nc18(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
-  else
-    e = launch_batch_nc32(sh.grid, sh.T, sh.smem, s, b.d_desc, b.d_items, sh.n_items, b.d_head, b.d_part_off, b.d_partials);
-  if (e != cudaSuccess) return e;
+  // the class with the most work on s, the others on the side branch: a class's blocks
+  // take the SMs that the other class's queue releases as it drains
+  int main_cls = -1;
+  double most = -1.0;
+  for (int c = 0; c < kClasses; c++) {
+    const double n = (double)(sh.cls_off[c + 1] - sh.cls_off[c]) * (double)kClassNc[c] * kClassNc[c];
+    if (sh.cls_off[c + 1] > sh.cls_off[c] && n > most) {
+      most = n;
+      main_cls = c;
+    }
+  }
+  bool forked = false;
+  for (int c = 0; c < kClasses; c++) {
+    if (c == main_cls || sh.cls_off[c + 1] == sh.cls_off[c]) continue;
+    if (!forked) {
+      if ((e = cudaEventRecord(b.fork, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(b.side, b.fork, 0)) != cudaSuccess) return e;
+      forked = true;
+    }
+    if ((e = launch_class(b, sh, c, b.side)) != cudaSuccess) return e;
+  }
+  if (main_cls >= 0 && (e = launch_class(b, sh, main_cls, s)) != cudaSuccess) return e;
+  if (forked) {
+    if ((e = cudaEventRecord(b.join, b.side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, b.join, 0)) != cudaSuccess) return e;
+  }
   batch_reduce<<<b.count, 256, 0, s>>>(b.d_partials, b.d_part_off, b.d_outs);
   return cudaGetLastError();
 }
@@ -222,6 +279,9 @@ void destroy(mhc_batch_s* b) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
 }
 
@@ -269,9 +329,12 @@ mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* p
   cudaMemcpy(b->d_kpref, kpref.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_nfam, nfam.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice);
   if (cudaMalloc(&b->d_desc, sizeof(FwdArgs) * count) != cudaSuccess ||
-      cudaMalloc(&b->d_head, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&b->d_head, sizeof(unsigned long long) * kClasses) != cudaSuccess ||
       cudaMalloc(&b->d_outs, sizeof(double*) * count) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
     destroy(b);
     set_error("mhc_batch_create: CUDA allocation failed");
     return MHC_ENOMEM;
@@ -309,7 +372,7 @@ mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* p
   mhc_status st = MHC_OK;
   for (int T : cands) {
     BatchShape sh = make_shape(*b, T);
-    if (sh.smem > 200 * 1024) {
+    if (max_smem(sh) > 200 * 1024) {
       b->tune_ms.push_back(-1.0);
       continue;
     }

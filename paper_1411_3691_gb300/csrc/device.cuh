@@ -549,15 +549,15 @@ __device__ __forceinline__ bool kfac_block12(const cd* __restrict__ S, int L, in
 // __syncwarp with the group's lane mask keep groups of one warp independent.
 // ------------------------------------------------------------------------------------
 
-// LU with partial pivoting of the R x C matrix B (shared memory, row pitch C), `steps`
+// LU with partial pivoting of the R x C matrix B (shared memory, row pitch P), `steps`
 // pivot columns.  Pivot: the largest |re| + |im| in the column, ties to the lowest row.
 // Rows are exchanged whole (multipliers included); perm[i] = original row at position i.
 // On return B holds the multipliers below, U above and the reciprocal pivots on the
 // diagonal.  Returns true when the pivot guard fires (a zero pivot, or binary exponents of
 // the pivots more than kp apart).
 template <int G>
-__device__ __forceinline__ bool group_lu(cd* B, int* perm, int R, int C, int steps, int g, unsigned gm,
-                                         int kp, cd* det_out, int* par_out) {
+__device__ __forceinline__ bool group_lu(cd* B, int P, int* perm, int R, int C, int steps, int g,
+                                         unsigned gm, int kp, cd* det_out, int* par_out) {
   for (int i = g; i < R; i += G) perm[i] = i;
   __syncwarp(gm);
   int parity = 0, emin = 4096, emax = -4096;
@@ -567,7 +567,7 @@ __device__ __forceinline__ bool group_lu(cd* B, int* perm, int R, int C, int ste
     double best = 0.0;
     int idx = -1;
     for (int i = k + g; i < R; i += G) {
-      const double m = abs1(B[i * C + k]);
+      const double m = abs1(B[i * P + k]);
       if (idx < 0 || gt_nonneg(m, best)) {
         best = m;
         idx = i;
@@ -584,9 +584,9 @@ __device__ __forceinline__ bool group_lu(cd* B, int* perm, int R, int C, int ste
     const int p = idx;
     if (p != k) {
       for (int u = g; u < C; u += G) {
-        const cd t = B[k * C + u];
-        B[k * C + u] = B[p * C + u];
-        B[p * C + u] = t;
+        const cd t = B[k * P + u];
+        B[k * P + u] = B[p * P + u];
+        B[p * P + u] = t;
       }
       if (g == 0) {
         const int t = perm[k];
@@ -596,7 +596,7 @@ __device__ __forceinline__ bool group_lu(cd* B, int* perm, int R, int C, int ste
       parity ^= 1;
     }
     __syncwarp(gm);
-    const cd piv = B[k * C + k];
+    const cd piv = B[k * P + k];
     const int e = expo(best);
     zero |= (__double_as_longlong(best) == 0);
     emin = min(emin, e);
@@ -604,18 +604,22 @@ __device__ __forceinline__ bool group_lu(cd* B, int* perm, int R, int C, int ste
     det = (k == 0) ? piv : cmul(det, piv);
     const cd rc = crcp(piv);
     for (int i = k + 1 + g; i < R; i += G) {
-      const cd l = cmul(B[i * C + k], rc);
-      B[i * C + k] = l;
-      for (int u = k + 1; u < C; u++) B[i * C + u] = cfms(l, B[k * C + u], B[i * C + u]);
+      const cd l = cmul(B[i * P + k], rc);
+      B[i * P + k] = l;
+      for (int u = k + 1; u < C; u++) B[i * P + u] = cfms(l, B[k * P + u], B[i * P + u]);
     }
     __syncwarp(gm);
-    if (g == 0) B[k * C + k] = rc;
+    if (g == 0) B[k * P + k] = rc;
   }
   __syncwarp(gm);
   *det_out = det;
   *par_out = parity;
   return steps > 0 && (zero || emax - emin > kp);
 }
+
+// Row pitch of a group's block in shared memory: odd, so that the G lanes of a group, which
+// work on rows i, i + 1, ..., i + G - 1 at the same column, hit distinct 16-byte bank groups.
+__device__ __forceinline__ int group_pitch(int C) { return C | 1; }
 
 // Group version of kfac_block (RHO = 1, 2) for the n > 6 blocks; same factor layout.
 // Bs: (NC-1)^2 complex scratch, Ws: NC-1 complex, Ps: NC-1 ints, all in shared memory.
@@ -626,34 +630,35 @@ __device__ __forceinline__ bool group_kfac_block(const cd* __restrict__ S, int L
                                                  int kp, int g, unsigned gm, cd* Bs, cd* Ws, int* Ps) {
   const int M = n - rho;
   const int C = rho == 2 ? M + 1 : M;
+  const int P = group_pitch(C);
   for (int e = g; e < M * C; e += G) {
     const int i = e / C, u = e - i * C;
-    Bs[e] = ldS(S + (size_t)arow[i] * L + scol[u]);
+    Bs[i * P + u] = ldS(S + (size_t)arow[i] * L + scol[u]);
   }
   __syncwarp(gm);
   cd det;
   int parity;
-  if (group_lu<G>(Bs, Ps, M, C, M, g, gm, kp, &det, &parity)) return true;
+  if (group_lu<G>(Bs, P, Ps, M, C, M, g, gm, kp, &det, &parity)) return true;
   const cd sd = parity ? cneg(det) : det;
   if (rho == 2) {  // w = -U1^{-1} u, u the transformed extra column
     for (int p = M - 1; p >= 0; p--) {
       cd s = make_double2(0.0, 0.0);
-      for (int q = p + 1 + g; q < M; q += G) s = cfma(Bs[p * C + q], Ws[q], s);
+      for (int q = p + 1 + g; q < M; q += G) s = cfma(Bs[p * P + q], Ws[q], s);
 #pragma unroll
       for (int off = 1; off < G; off <<= 1) {
         s.x += __shfl_xor_sync(gm, s.x, off);
         s.y += __shfl_xor_sync(gm, s.y, off);
       }
       if (g == 0) {
-        const cd b = Bs[p * C + M];
-        Ws[p] = cmul(make_double2(b.x + s.x, b.y + s.y), cneg(Bs[p * C + p]));
+        const cd b = Bs[p * P + M];
+        Ws[p] = cmul(make_double2(b.x + s.x, b.y + s.y), cneg(Bs[p * P + p]));
       }
       __syncwarp(gm);
     }
   }
   for (int e = g; e < M * M; e += G) {
     const int i = e / M, u = e - i * M;
-    K[e] = Bs[i * C + u];
+    K[e] = Bs[i * P + u];
   }
   for (int i = g; i < M; i += G) K[M * M + i] = make_double2((double)Ps[i], 0.0);
   if (rho == 1) {
@@ -676,15 +681,19 @@ __device__ __forceinline__ bool group_kfac_block12(const cd* __restrict__ S, int
                                                    const int32_t* __restrict__ scol, cd* __restrict__ K,
                                                    int kp, int g, unsigned gm, cd* Bs, int* Ps) {
   const int M = n - 1, C = n - 2;
+  const int P = group_pitch(C);
   for (int e = g; e < M * C; e += G) {
     const int i = e / C, u = e - i * C;
-    Bs[e] = ldS(S + (size_t)arow[i] * L + scol[u]);
+    Bs[i * P + u] = ldS(S + (size_t)arow[i] * L + scol[u]);
   }
   __syncwarp(gm);
   cd det;
   int parity;
-  if (group_lu<G>(Bs, Ps, M, C, C, g, gm, kp, &det, &parity)) return true;
-  for (int e = g; e < M * C; e += G) K[e] = Bs[e];
+  if (group_lu<G>(Bs, P, Ps, M, C, C, g, gm, kp, &det, &parity)) return true;
+  for (int e = g; e < M * C; e += G) {
+    const int i = e / C, u = e - i * C;
+    K[e] = Bs[i * P + u];
+  }
   for (int i = g; i < M; i += G) K[M * C + i] = make_double2((double)Ps[i], 0.0);
   if (g == 0) K[M * C + M] = parity ? cneg(det) : det;
   __syncwarp(gm);

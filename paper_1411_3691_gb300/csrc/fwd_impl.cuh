@@ -338,7 +338,10 @@ template <int NCMAX>
 struct KGroup {
   static constexpr int G = NCMAX <= 18 ? 4 : 16;              // lanes per block
   static constexpr int GPW = 32 / G;                           // blocks per warp
-  static constexpr int BS = (NCMAX - 1) * (NCMAX - 1) + (NCMAX - 1);  // complex per block
+  // complex per block (matrix + back-substitution vector), padded to 4 mod 8 16-byte units
+  // so that two groups sharing an 8-lane shared-memory phase use disjoint bank groups
+  static constexpr int RAW = (NCMAX - 1) * (NCMAX - 1) + (NCMAX - 1);
+  static constexpr int BS = RAW + ((4 - RAW % 8) + 8) % 8;
   static constexpr int PS = NCMAX;                             // ints per block
   static constexpr size_t smem() { return (size_t)GPW * (BS * sizeof(double2) + PS * sizeof(int)); }
 };
