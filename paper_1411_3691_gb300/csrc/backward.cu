@@ -156,8 +156,8 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   // one warp per block: the per-sink state (cached solves, member determinants, weight
   // accumulators) is all that lives in shared memory, so several warps fit per SM
   const int T = 32;
-  // cached solves [ysl][t] | member dets [F][kmax][t + 1] | dw_src accumulators [kmax][t]
-  auto smem_of = [&](int t) { return ((size_t)(ysl + kmax) * t + (size_t)kmax * F * (t + 1)) * sizeof(double2); };
+  // cached solves [ysl][t] | member dets [F][kmax][t + 1]
+  auto smem_of = [&](int t) { return ((size_t)ysl * t + (size_t)kmax * F * (t + 1)) * sizeof(double2); };
   if (smem_of(T) > 220 * 1024) {
     set_error("mhc_correlator_backward: a family is too large for the adjoint's shared memory; "
               "plan with a smaller opts.max_family");
@@ -186,6 +186,9 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
     return st;
   if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_stage), (size_t)ctas * T * mn_max,
                       &d.bwd_stage_bytes)) != MHC_OK)
+    return st;
+  if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_accs), (size_t)ctas * kmax * T,
+                      &d.bwd_accs_bytes)) != MHC_OK)
     return st;
   // row-label index of the accumulators, per flavour: label -> (family, slot) pairs
   if (d.bwd_index.empty()) {
@@ -236,6 +239,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.dwsrc_part = reinterpret_cast<double2*>(d.bwd_wsrc);
   b.dwsnk_part = reinterpret_cast<double2*>(d.bwd_wsnk);
   b.stage = reinterpret_cast<double2*>(d.bwd_stage);
+  b.accs = reinterpret_cast<double2*>(d.bwd_accs);
   const int nc = plan_ncmax(p);
   b.kinv = nullptr;
   if (b.a.snk_orig) {  // two-sided blocks: the factors of B, then B^{-1} for the cofactors

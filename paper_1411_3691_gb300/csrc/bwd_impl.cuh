@@ -31,6 +31,7 @@ struct BwdArgs {
   double2* dwsrc_part;  // [member][n_chunks]
   double2* dwsnk_part;  // [W][n_snk]
   double2* stage;       // [cta][T][mn_max] shared-row cofactors of each sink, per block
+  double2* accs;        // [cta][kmax][T] dw_src accumulators of each sink, per block
   const double2* kinv;  // [W][Q][kistride]: B^{-1} row-major per flavour (two-sided blocks)
   int kistride;
   int kioff[MHC_FMAX];
@@ -477,7 +478,7 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
 }
 
 template <int NCMAX>
-__global__ void __launch_bounds__(32, 1) bwd_kernel(const BwdArgs B) {
+__global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
   const FwdArgs& a = B.a;
   extern __shared__ double2 smem[];
   const int T = blockDim.x;
@@ -485,10 +486,12 @@ __global__ void __launch_bounds__(32, 1) bwd_kernel(const BwdArgs B) {
   const int cta = blockIdx.x;
   const int W = cta / B.n_chunks, chunk = cta % B.n_chunks;
   const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
-  // shared memory: y cache | dets [c][f] | dw_src accumulators [c] | staging [warp][lane][M n]
+  // shared memory: y cache [ysl][T] | member dets [F][kmax][T + 1]
   cd* Ysm = smem;
   cd* Dets = Ysm + (size_t)B.ysl * T;
-  cd* AccS = Dets + (size_t)B.kmax * a.F * (T + 1);
+  // dw_src accumulators: global scratch of this block (L1/L2-resident), which leaves the
+  // shared memory to the data the scatter shares across lanes
+  cd* AccS = B.accs + (size_t)cta * B.kmax * T;
   // staging of the shared-row cofactors: global scratch of this block (L1 resident)
   cd* Stage = B.stage + (size_t)cta * T * B.mn_max;
   cd* myStage = Stage + (size_t)(warp * 32 + lane) * B.mn_max;

@@ -43,6 +43,8 @@ struct DevicePlan {
   int32_t* kguard = nullptr;     // [W][Q][F] 1: the block's pivot guard fired
   double* bwd_stage = nullptr;   // [cta][T][mn_max] adjoint staging
   size_t bwd_stage_bytes = 0;
+  double* bwd_accs = nullptr;    // [cta][kmax][T] adjoint dw_src accumulators
+  size_t bwd_accs_bytes = 0;
   double* kinv = nullptr;        // [W][Q][sum_f (n_f-1)^2] B^{-1} of two-sided blocks (adjoint)
   size_t kinv_bytes = 0;
   int kstride = 0;

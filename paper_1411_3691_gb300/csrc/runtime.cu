@@ -43,7 +43,8 @@ void free_device(DevicePlan& d) {
   void* ptrs[] = {d.fam_info, d.fam_rank, d.fam_arow, d.mem_term, d.mem_par, d.mem_lab,
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
-                  d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard, d.kinv, d.bwd_stage};
+                  d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard, d.kinv, d.bwd_stage,
+                  d.bwd_accs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& bi : d.bwd_index) {
