@@ -54,3 +54,49 @@ def test_batch_matches_oracle_and_plain(M):
     for p in plans:
         M.mhc_get_status(p.handle)
     M.mhc_batch_destroy(batch)
+
+
+def test_full_batch_64_correlators(M):
+    """The 64-correlator batch of the benchmark, in its launch configuration (autotuned tile,
+    per-class persistent kernels, CUDA graph).  Correlators of at most 5e6 pairs and n_f <= 9:
+    C against the oracle.  Every correlator: C against one mhc_correlator call of the same
+    plan, within 1e-10 of a scale sum |w w prod det| that the oracle estimates from 2000
+    seeded pairs (exact for the small ones); and 200 seeded pairs through the per-pair probe
+    against the oracle's determinants."""
+    items = wl.batch(64)
+    plans = [M.Plan.from_workload(w) for w in items]
+    S = [[torch.from_numpy(s).cuda() for s in w.S] for w in items]
+    batch = M.mhc_batch_create([p.handle for p in plans])
+    outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in items]
+    M.mhc_batch_correlator(batch, S, outs)
+    torch.cuda.synchronize()
+    got = [complex(*o.cpu().numpy()) for o in outs]
+    rng = np.random.default_rng(64)
+    n_oracle = 0
+    for k, w in enumerate(items):
+        plain = complex(*plans[k].correlator(S[k]).cpu().numpy())
+        ns, nk = len(w.w_src), len(w.w_snk)
+        if w.pairs <= 5_000_000 and max(w.n_f) <= 9:
+            ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk,
+                                           threads=16)
+            assert abs(got[k] - ref) <= 1e-11 * scale, (k, w.n_f, got[k], ref)
+            n_oracle += 1
+        else:
+            ii = rng.integers(0, ns, 2000)
+            jj = rng.integers(0, nk, 2000)
+            d = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj)
+            terms = np.abs(w.w_src[ii] * w.w_snk[jj] * np.prod(d, axis=1))
+            scale = float(np.mean(terms)) * w.pairs
+        assert abs(got[k] - plain) <= 1e-10 * scale, (k, w.n_f, got[k], plain)
+        ii = rng.integers(0, ns, 200)
+        jj = rng.integers(0, nk, 200)
+        gd = plans[k].pair_dets(S[k], torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()).cpu().numpy()
+        rd = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj)
+        for f, n in enumerate(w.n_f):
+            err = np.abs(gd[:, f] - rd[:, f])
+            assert np.all(err <= 1e-9 * np.abs(rd[:, f]) + 1e-300), (k, f, float(np.max(err / np.abs(rd[:, f]))))
+        M.mhc_get_status(plans[k].handle)
+    assert n_oracle >= 8
+    M.mhc_batch_destroy(batch)
+    for p in plans:
+        p.close()
