@@ -27,24 +27,137 @@ struct QEntry {
   double pad2;
 };
 
+// Fresh determinants of a group of queued pairs that share member m and a two-sided sink
+// family Q with one changed column (flavour f, rank-1 family): their matrices agree in the
+// first n - 1 columns (the family's shared rows and member row against the sink family's
+// shared columns) and differ in the last.  Partial-pivot LU eliminates column by column, so
+// the pivots and multipliers of the first n - 1 columns are common to the group: the warp
+// factorises them once (lane i holds row i), then every lane of the group carries its own
+// sink's last column through the same steps -- the arithmetic of a fresh LU per pair at
+// O(n^2) per pair instead of O(n^3).  Called by the whole warp; returns the determinant on
+// the lanes in grp.
+template <int NC>
+__device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, int m, int Q, int64_t j,
+                                               unsigned grp) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int n = a.n_f[f];
+  const int L = a.L_f[f];
+  const dev::cd* S = a.S[f];
+  const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+  const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
+  // lane i < n: row i of the n x (n - 1) block (rows: shared rows, then the member's row)
+  const int rlab = lane < n - 1 ? arow[lane] : a.mem_lab[((int64_t)m * a.F + f) * 2];
+  dev::cd R[NC];
+#pragma unroll
+  for (int u = 0; u < NC - 1; u++)
+    R[u] = (lane < n && u < n - 1) ? dev::ldS(S + (size_t)rlab * L + scol[u]) : make_double2(0.0, 0.0);
+  // this lane's sink: its last column, entries in row order 0..n-1
+  const bool mine = (grp >> lane) & 1;
+  dev::cd c[NC];
+  const int lc = mine ? dev::sink_cols(a, j)[a.off_f[f] + n - 1] : 0;
+#pragma unroll
+  for (int i = 0; i < NC; i++) {
+    const int li = i < n - 1 ? arow[i < n - 1 ? i : 0] : a.mem_lab[((int64_t)m * a.F + f) * 2];
+    c[i] = (mine && i < n) ? dev::ldS(S + (size_t)li * L + lc) : make_double2(0.0, 0.0);
+  }
+  unsigned piv = 0;  // rows already used as pivots
+  int parity = 0;
+  bool zero = false;
+  dev::cd det = make_double2(1.0, 0.0);
+#pragma unroll
+  for (int k = 0; k < NC - 1; k++) {
+    if (k >= n - 1) break;
+    // pivot: the largest |re| + |im| in column k among the unused rows, lowest row on ties
+    const bool cand = lane < n && !((piv >> lane) & 1);
+    double best = cand ? dev::abs1(R[k]) : -1.0;
+    int idx = cand ? lane : 64;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(FULL, best, o);
+      const int oi = __shfl_xor_sync(FULL, idx, o);
+      const bool take = ob > best || (ob == best && oi < idx);
+      best = take ? ob : best;
+      idx = take ? oi : idx;
+    }
+    const int p = idx;
+    // the permutation's parity: p moves ahead of the unused rows that precede it
+    parity ^= __popc(~piv & ((1u << p) - 1u) & ((1u << n) - 1u)) & 1;
+    piv |= 1u << p;
+    zero |= best == 0.0;
+    const dev::cd pk = make_double2(__shfl_sync(FULL, R[k].x, p), __shfl_sync(FULL, R[k].y, p));
+    det = (k == 0) ? pk : dev::cmul(det, pk);
+    const dev::cd rc = dev::crcp(pk);
+    // multipliers of the unused rows; the group's last columns follow
+    const bool act = lane < n && !((piv >> lane) & 1);
+    const dev::cd l = dev::cmul(R[k], rc);
+#pragma unroll
+    for (int u = k + 1; u < NC - 1; u++) {
+      if (u >= n - 1) break;
+      const dev::cd pu = make_double2(__shfl_sync(FULL, R[u].x, p), __shfl_sync(FULL, R[u].y, p));
+      if (act) R[u] = dev::cfms(l, pu, R[u]);
+    }
+    // last column of each sink: row i -= l_i * (pivot row's entry)
+    dev::cd vp = c[0];
+#pragma unroll
+    for (int i = 1; i < NC; i++) vp = i == p ? c[i] : vp;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+      if (i >= n) break;
+      const dev::cd li = make_double2(__shfl_sync(FULL, l.x, i), __shfl_sync(FULL, l.y, i));
+      if (!((piv >> i) & 1)) c[i] = dev::cfms(li, vp, c[i]);
+    }
+  }
+  // the remaining row holds the last pivot
+  const int last = __ffs(~piv & ((1u << n) - 1u)) - 1;
+  dev::cd vl = c[0];
+#pragma unroll
+  for (int i = 1; i < NC; i++) vl = i == last ? c[i] : vl;
+  zero |= __double_as_longlong(dev::abs1(vl)) == 0;
+  det = n == 1 ? vl : dev::cmul(det, vl);
+  if (zero) return make_double2(0.0, 0.0);
+  return parity ? dev::cneg(det) : det;
+}
+
+// Refactor the queued pairs: the lane's product of the flavours that passed, times fresh
+// determinants of the flavours that failed.  Pairs that share a member and a two-sided
+// sink family (one changed column, rank-1 family) are factorised together (group_fresh);
+// the others one per lane.  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
                               double2& acc) {
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  if (lane < count) {
-    const QEntry e = q[lane];
-    const int64_t j = jbase + e.lane;
-    const int32_t* cols = dev::sink_cols(a, j);
-    double2 prod = e.prod;
-    int32_t rows[NCMAX];
-    for (int f = 0; f < a.F; f++) {
-      if (!((e.fail >> f) & 1)) continue;
-      const int n = a.n_f[f];
-      const int rho = a.fam_rank[(int64_t)W * a.F + f];
-      dev::member_rows(a, W, e.member, f, rho, rows);
+  const bool have = lane < count;
+  QEntry e = {};
+  if (have) e = q[lane];
+  const int64_t j = jbase + (have ? e.lane : 0);
+  const int32_t* cols = dev::sink_cols(a, j);
+  double2 prod = have ? e.prod : make_double2(1.0, 0.0);
+  const int Q = a.snk_orig ? a.snk_q[j] : -1;
+  int32_t rows[NCMAX];
+  for (int f = 0; f < a.F; f++) {
+    const bool need = have && ((e.fail >> f) & 1);
+    const int n = a.n_f[f];
+    const bool grouped = need && NCMAX <= 18 && n >= 2 && a.fam_rank[(int64_t)W * a.F + f] == 1 && Q >= 0 &&
+                         a.q_two[Q] && a.q_rank[(int64_t)Q * a.F + f] == 1;
+    unsigned todo = __ballot_sync(FULL, grouped);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int lm = __shfl_sync(FULL, have ? e.member : 0, leader);
+      const int lq = __shfl_sync(FULL, Q, leader);
+      const unsigned grp = __ballot_sync(FULL, ((todo >> lane) & 1) && e.member == lm && Q == lq);
+      const double2 d = group_fresh<NCMAX <= 18 ? NCMAX : 18>(a, W, f, lm, lq, j, grp);
+      if ((grp >> lane) & 1) prod = dev::cmul(prod, d);
+      todo &= ~grp;
+    }
+    if (need && !grouped) {
+      dev::member_rows(a, W, e.member, f, a.fam_rank[(int64_t)W * a.F + f], rows);
       const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, cols + a.off_f[f]);
       prod = dev::cmul(prod, d);
     }
+  }
+  if (have) {
     acc.x = fma(e.w, prod.x, acc.x);
     acc.y = fma(e.w, prod.y, acc.y);
   }
