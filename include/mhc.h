@@ -203,7 +203,10 @@ mhc_status mhc_correlator(mhc_plan_t plan, const double* const* S_f, const doubl
  * which is PyTorch's convention for the gradient of a real loss.  g_out_dev is a device
  * pointer to 2 doubles.  Any of dS_f (the whole array or single entries), dw_src_dev or
  * dw_snk_dev may be NULL to skip that output.  The dS_f buffers must not alias each
- * other.
+ * other.  Two-row (rank-2) families are differentiated through the null vectors of their
+ * shared rows; when those rows fail the pivot guard for some sink, that block's dS_f
+ * contribution is left out and mhc_get_status returns MHC_EUNSUPPORTED (plan with
+ * opts->rank2 = 0 for such inputs).  Not in the paper.
  */
 mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
                                    const double* w_src_dev, const double* w_snk_dev,

@@ -131,22 +131,17 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
     return MHC_EINVAL;
   }
   Plan& p = *reinterpret_cast<Plan*>(plan);
+  bool any_r2 = false;  // two-row families: two member rows per member, coefficient scratch
   for (int64_t W = 0; W < p.n_fam; W++)
-    for (int f = 0; f < p.F; f++)
-      if (p.fam_rank[W * p.F + f] == 2) {
-        set_error("mhc_correlator_backward: the adjoint of rank-2 families is not built; "
-                  "plan with opts.rank2 = 0");
-        return MHC_EUNSUPPORTED;
-      }
+    for (int f = 0; f < p.F; f++) any_r2 |= p.fam_rank[W * p.F + f] == 2;
   mhc_status st = ensure_device(p);
   if (st != MHC_OK) return st;
   BwdArgs b;
   if ((st = fill_fwd_args(p, S_f, w_src_dev, w_snk_dev, b.a)) != MHC_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int F = p.F;
-  int ysl = 0, mn_max = 1, Mmax = 0, Lmax = 1;
+  int ysl = b.a.slots, mn_max = 1, Mmax = 0, Lmax = 1;  // ysl: the cached solves' slots
   for (int f = 0; f < F; f++) {
-    ysl += p.n_f[f];
     mn_max = std::max(mn_max, std::max(p.n_f[f] - 1, 0) * p.n_f[f]);
     Mmax = std::max(Mmax, p.n_f[f] - 1);
     Lmax = std::max(Lmax, (int)p.L_f[f]);
@@ -166,7 +161,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   const size_t smem = smem_of(T);
   const int warps = T / 32;
   const int n_tiles = (int)((p.n_snk + T - 1) / T);
-  const int slots_max = Mmax + kmax;
+  const int slots_max = Mmax + (any_r2 ? 2 : 1) * kmax;
   const size_t per_cta = (size_t)warps * F * slots_max * Lmax * sizeof(double2);
   int n_chunks = (int)std::min<int64_t>(n_tiles, std::max<int64_t>(1, (48 * 152 + p.n_fam - 1) / p.n_fam));
   while (n_chunks > 1 && (double)per_cta * p.n_fam * n_chunks > 1.0e9) n_chunks = (n_chunks + 1) / 2;
@@ -190,6 +185,9 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_accs), (size_t)ctas * kmax * T,
                       &d.bwd_accs_bytes)) != MHC_OK)
     return st;
+  if (any_r2 && (st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_r2), (size_t)ctas * kmax * 4 * T,
+                                &d.bwd_r2_bytes)) != MHC_OK)
+    return st;
   // row-label index of the accumulators, per flavour: label -> (family, slot) pairs
   if (d.bwd_index.empty()) {
     d.bwd_index.resize(F);
@@ -198,10 +196,13 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
       std::vector<std::vector<std::pair<int, int>>> lists(L);
       if (n > 0) {
         for (int64_t W = 0; W < p.n_fam; W++) {
-          for (int m = 0; m < n - 1; m++) lists[p.fam_arow[W * p.Tn + p.off_f[f] + m]].push_back({(int)W, m});
+          // slots: shared rows m < n - rho, then the member rows (two per member, rank 2)
+          const int rho = p.fam_rank[W * F + f];
+          for (int m = 0; m < n - rho; m++) lists[p.fam_arow[W * p.Tn + p.off_f[f] + m]].push_back({(int)W, m});
           for (int64_t c = 0; c < p.fam_off[W + 1] - p.fam_off[W]; c++) {
             const int64_t mm = p.fam_off[W] + c;
-            lists[p.mem_lab[(mm * F + f) * 2]].push_back({(int)W, (int)(n - 1 + c)});
+            for (int t = 0; t < rho; t++)
+              lists[p.mem_lab[(mm * F + f) * 2 + t]].push_back({(int)W, (int)(n - rho + rho * c + t)});
           }
         }
       }
@@ -230,16 +231,13 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.Lmax = Lmax;
   b.mn_max = mn_max;
   b.ysl = ysl;
-  b.a.n_tiles = n_tiles;
-  for (int f = 0, o = 0; f < F; f++) {
-    b.a.yoff[f] = o;
-    o += p.n_f[f];
-  }
+  b.a.n_tiles = n_tiles;  // the cached-solve layout (a.yoff, a.slots) stays the forward's
   b.dS_part = reinterpret_cast<double2*>(d.bwd_rows);
   b.dwsrc_part = reinterpret_cast<double2*>(d.bwd_wsrc);
   b.dwsnk_part = reinterpret_cast<double2*>(d.bwd_wsnk);
   b.stage = reinterpret_cast<double2*>(d.bwd_stage);
   b.accs = reinterpret_cast<double2*>(d.bwd_accs);
+  b.r2 = reinterpret_cast<double2*>(d.bwd_r2);
   const int nc = plan_ncmax(p);
   b.kinv = nullptr;
   if (b.a.snk_orig) {  // two-sided blocks: the factors of B, then B^{-1} for the cofactors

@@ -32,6 +32,7 @@ struct BwdArgs {
   double2* dwsnk_part;  // [W][n_snk]
   double2* stage;       // [cta][T][mn_max] shared-row cofactors of each sink, per block
   double2* accs;        // [cta][kmax][T] dw_src accumulators of each sink, per block
+  double2* r2;          // [cta][kmax][4][T] member-row coefficients of two-row families
   const double2* kinv;  // [W][Q][kistride]: B^{-1} row-major per flavour (two-sided blocks)
   int kistride;
   int kioff[MHC_FMAX];
@@ -347,6 +348,226 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
   }
 }
 
+// Two-row family (rank 2), shared rows A ((n-2) x n), member rows b1, b2: G = [A; b1; b2].
+// With the null vectors z1, z2 of A (last two coordinates the identity), sd = sign(P)
+// det(A1) and D = [b1; b2] [z1 z2], det G = sd det(D), and Jacobi's formula gives
+//   cof(G)[b1] = sd (z1 D11 - z2 D10),   cof(G)[b2] = sd (z2 D00 - z1 D01),
+//   sum_c gamma_c cof(G_c)[A] = sd X0^T (s I - E Z^T),
+// X0 = [A1^{-1}; 0; 0] (a right inverse of A), s = sum_c gamma_c det(D_c),
+// E = sum_c gamma_c [b1 b2] adj(D_c)^T (n x 2): row m of the shared block is
+//   sd [ s (u_m; 0; 0) - (u_m . E0) z1 - (u_m . E1) z2 ],  u_m = A1^{-1} e_m,
+// O(n) per member and no division by det G.  Writes the shared block to Mst (row-major
+// (n-2) x n) and the member rows' coefficients on (z1, z2) -- gamma sd (D11, -D10) for
+// b1, gamma sd (-D01, D00) for b2 -- to R2[c][4][T].  When the shared rows fail the pivot
+// guard the block is not differentiated: the outputs are zero and the status reports it.
+template <int NC>
+__device__ __noinline__ void cof_pass2(const FwdArgs& a, int f, int n, int mem0, int kW, double wj,
+                                       int tid, int T, int kmax, const int32_t* __restrict__ col,
+                                       const int32_t* __restrict__ arow, const cd* Dets, const cd* Y,
+                                       bool guarded, cd* Mst, cd* R2) {
+  const int M = n - 2;
+  const cd* S = a.S[f];
+  const int L = a.L_f[f];
+  const cd sd = Y[(size_t)2 * n * T];
+  cd E0[NC], E1[NC];
+  for (int q = 0; q < n; q++) E0[q] = E1[q] = make_double2(0.0, 0.0);
+  cd s = make_double2(0.0, 0.0);
+  for (int c = 0; c < kW; c++) {
+    const int m = mem0 + c;
+    double wc = a.w_src[a.mem_term[m]] * wj;
+    if (__popc(a.mem_par[m]) & 1) wc = -wc;
+    cd g = make_double2(wc, 0.0);
+    for (int f2 = 0; f2 < a.F; f2++)
+      if (f2 != f) g = dev::cmul(g, Dets[dix(c, f2, kmax, T, tid)]);
+    const cd* r1 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
+    const cd* r2 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2 + 1] * L;
+    cd d00 = make_double2(0.0, 0.0), d01 = d00, d10 = d00, d11 = d00;
+    for (int q = 0; q < n; q++) {
+      const cd b1 = dev::ldS(r1 + col[q]), b2 = dev::ldS(r2 + col[q]);
+      const cd z1 = Y[(size_t)q * T], z2 = Y[(size_t)(n + q) * T];
+      d00 = dev::cfma(b1, z1, d00);
+      d01 = dev::cfma(b1, z2, d01);
+      d10 = dev::cfma(b2, z1, d10);
+      d11 = dev::cfma(b2, z2, d11);
+    }
+    s = dev::cfma(g, dev::cfms(d01, d10, dev::cmul(d00, d11)), s);
+    const cd g00 = dev::cmul(g, d00), g01 = dev::cmul(g, d01), g10 = dev::cmul(g, d10), g11 = dev::cmul(g, d11);
+    for (int q = 0; q < n; q++) {
+      const cd b1 = dev::ldS(r1 + col[q]), b2 = dev::ldS(r2 + col[q]);
+      E0[q] = dev::cfms(b2, g01, dev::cfma(b1, g11, E0[q]));
+      E1[q] = dev::cfms(b1, g10, dev::cfma(b2, g00, E1[q]));
+    }
+    const cd gs = dev::cmul(g, sd);
+    cd* R = R2 + (size_t)c * 4 * T + tid;
+    R[0] = guarded ? make_double2(0.0, 0.0) : dev::cmul(gs, d11);
+    R[(size_t)T] = guarded ? make_double2(0.0, 0.0) : dev::cneg(dev::cmul(gs, d10));
+    R[(size_t)2 * T] = guarded ? make_double2(0.0, 0.0) : dev::cneg(dev::cmul(gs, d01));
+    R[(size_t)3 * T] = guarded ? make_double2(0.0, 0.0) : dev::cmul(gs, d00);
+  }
+  // LU of A1 (the shared rows on the first n - 2 columns), partial pivoting
+  constexpr int MC = NC - 2 > 0 ? NC - 2 : 1;
+  cd A[MC][MC];
+  int perm[MC];
+  for (int i = 0; i < M; i++) {
+    perm[i] = i;
+    const cd* row = S + (size_t)arow[i] * L;
+    for (int q = 0; q < M; q++) A[i][q] = dev::ldS(row + col[q]);
+  }
+  int emin = 4096, emax = -4096;
+  bool zero = false;
+  cd rc[MC];
+  for (int k = 0; k < M; k++) {
+    double best = dev::abs1(A[k][k]);
+    int p = k;
+    for (int i = k + 1; i < M; i++) {
+      const double v = dev::abs1(A[i][k]);
+      if (dev::gt_nonneg(v, best)) {
+        best = v;
+        p = i;
+      }
+    }
+    if (p != k) {
+      for (int q = 0; q < M; q++) {
+        const cd t = A[k][q];
+        A[k][q] = A[p][q];
+        A[p][q] = t;
+      }
+      const int t = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t;
+    }
+    const int e = dev::expo(best);
+    zero |= (__double_as_longlong(best) == 0);
+    emin = min(emin, e);
+    emax = max(emax, e);
+    rc[k] = dev::crcp(A[k][k]);
+    for (int i = k + 1; i < M; i++) {
+      const cd l = dev::cmul(A[i][k], rc[k]);
+      A[i][k] = l;
+      for (int q = k + 1; q < M; q++) A[i][q] = dev::cfms(l, A[k][q], A[i][q]);
+    }
+  }
+  if (guarded || (M > 0 && (zero || emax - emin > a.kp))) {
+    atomicOr(&a.counters[0], kStatusUnsupported);
+    for (int e = 0; e < M * n; e++) Mst[e] = make_double2(0.0, 0.0);
+    for (int c = 0; c < kW; c++)
+      for (int t = 0; t < 4; t++) R2[((size_t)c * 4 + t) * T + tid] = make_double2(0.0, 0.0);
+    return;
+  }
+  for (int i = 0; i < M; i++) {  // u = column perm[i] of A1^{-1} = U^{-1} L^{-1} e_i
+    cd u[MC];
+    for (int p = 0; p < M; p++) {
+      if (p < i) {
+        u[p] = make_double2(0.0, 0.0);
+      } else if (p == i) {
+        u[p] = make_double2(1.0, 0.0);
+      } else {
+        cd w = dev::cneg(A[p][i]);
+        for (int t = i + 1; t < p; t++) w = dev::cfms(A[p][t], u[t], w);
+        u[p] = w;
+      }
+    }
+    for (int p = M - 1; p >= 0; p--) {
+      cd w = u[p];
+      for (int t = p + 1; t < M; t++) w = dev::cfms(A[p][t], u[t], w);
+      u[p] = dev::cmul(w, rc[p]);
+    }
+    cd e0 = make_double2(0.0, 0.0), e1 = e0;
+    for (int q = 0; q < M; q++) {
+      e0 = dev::cfma(u[q], E0[q], e0);
+      e1 = dev::cfma(u[q], E1[q], e1);
+    }
+    const cd se0 = dev::cmul(sd, e0), se1 = dev::cmul(sd, e1), ss = dev::cmul(sd, s);
+    cd* row = Mst + (size_t)perm[i] * n;
+    for (int q = 0; q < M; q++) {
+      const cd z1 = Y[(size_t)q * T], z2 = Y[(size_t)(n + q) * T];
+      row[q] = dev::cfms(se1, z2, dev::cfms(se0, z1, dev::cmul(ss, u[q])));
+    }
+    row[M] = dev::cneg(se0);
+    row[M + 1] = dev::cneg(se1);
+  }
+}
+
+// Scatter of one warp's sinks for a two-row family (flavour f): lane s owns row s -- a
+// shared row (s < n - 2, from the staged block) or member (s - n + 2) / 2's first or
+// second changed row, whose values are coefficient combinations of the cached z1, z2.
+// Same fixed order and shared-column sums as scatter_rows.
+template <int NC>
+__device__ __noinline__ void scatter_rows2(const FwdArgs& a, const BwdArgs& B, int f, int n, int kW,
+                                           int nlive, int T, int warp, int lane,
+                                           const int32_t* __restrict__ mycol, int myQ, int mynsh,
+                                           const cd* Stage, const cd* Ysm, const cd* R2, cd* Df) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int M = n - 2;
+  const int nslots = M + 2 * kW;
+  int cl[NC];
+#pragma unroll
+  for (int q = 0; q < NC; q++) cl[q] = q < n ? mycol[q] : 0;
+  for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
+    const bool act = s < nslots;
+    const bool mem = s >= M;
+    const int c = act && mem ? (s - M) >> 1 : 0;
+    const int t = act && mem ? (s - M) & 1 : 0;
+    cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
+    cd acc[NC];
+    int curlab[NC];
+    int curQ = -2, nsh = 0;
+#pragma unroll
+    for (int q = 0; q < NC; q++) {
+      acc[q] = make_double2(0.0, 0.0);
+      curlab[q] = 0;
+    }
+    for (int jl = 0; jl <= nlive; jl++) {
+      const bool live = jl < nlive;
+      const int src = jl & 31;
+      const int Qj = __shfl_sync(FULL, myQ, src);
+      const int nsj = __shfl_sync(FULL, mynsh, src);
+      int cj[NC];
+#pragma unroll
+      for (int q = 0; q < NC; q++) cj[q] = __shfl_sync(FULL, cl[q], src);
+      if (!live || Qj != curQ || Qj < 0) {
+        if (act) {
+#pragma unroll
+          for (int q = 0; q < NC; q++)
+            if (q < nsh) {
+              cd& d = Drow[curlab[q]];
+              d.x += acc[q].x;
+              d.y += acc[q].y;
+            }
+        }
+        if (!live) break;
+        curQ = Qj;
+        nsh = nsj;
+#pragma unroll
+        for (int q = 0; q < NC; q++) {
+          acc[q] = make_double2(0.0, 0.0);
+          curlab[q] = cj[q];
+        }
+      }
+      const int ts = warp * 32 + jl;
+      cd k0 = make_double2(0.0, 0.0), k1 = k0;
+      if (mem) {
+        k0 = R2[((size_t)c * 4 + 2 * t) * T + ts];
+        k1 = R2[((size_t)c * 4 + 2 * t + 1) * T + ts];
+      }
+      const cd* st = Stage + (size_t)ts * B.mn_max + (mem ? 0 : s * n);
+#pragma unroll
+      for (int q = 0; q < NC; q++) {
+        if (q >= n) break;
+        const cd v = mem ? dev::cfma(k1, Ysm[(size_t)(a.yoff[f] + n + q) * T + ts],
+                                     dev::cmul(k0, Ysm[(size_t)(a.yoff[f] + q) * T + ts]))
+                         : st[q];
+        if (q < nsh) {
+          acc[q] = dev::cadd(acc[q], v);
+        } else if (act) {
+          cd& d = Drow[cj[q]];
+          d = dev::cadd(d, v);
+        }
+      }
+    }
+  }
+}
+
 template <int NCMAX>
 __device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n, int W,
                                                   int mem0, int kW, double wj, int tid, int T,
@@ -523,17 +744,22 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       ey[f] = 0;
       if (n == 0) continue;
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
-      if (qtwo && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
-        // two-sided block: y from the stored factors of B (see kapply / kapply12)
+      const int rho = a.fam_rank[(int64_t)W * a.F + f];
+      const int sig = qtwo ? a.q_rank[(int64_t)Q * a.F + f] : 0;
+      if (qtwo && (rho == 1 || sig == 1) && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+        // two-sided block: y (z1, z2 for two-row families) from the stored factors
         const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
-        if (a.q_rank[(int64_t)Q * a.F + f] == 2)
+        if (rho == 2)
+          dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                       Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+        else if (sig == 2)
           dev::dispatch_kapply12<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
                                         Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
         else
           dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
                                       Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
       } else {
-        const bool g = dev::dispatch_shared<NCMAX>(n, 1, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
+        const bool g = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
                                                    Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f], a.kp);
         pguard |= (unsigned)g << f;
       }
@@ -548,11 +774,12 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
         if (n > 0) {
           bool fail = (pguard >> f) & 1;
           const int32_t* col = cols + a.off_f[f];
+          const int rho = a.fam_rank[(int64_t)W * a.F + f];
           if (!fail)
-            d = dev::dispatch_member<NCMAX>(n, 1, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
+            d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
                                             col, Ysm + (size_t)a.yoff[f] * T + tid, T, ey[f], a.kc, &fail);
           if (fail) {
-            dev::member_rows(a, W, m, f, 1, rows);
+            dev::member_rows(a, W, m, f, rho, rows);
             d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, col);
           }
         }
@@ -577,6 +804,21 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int M = n - 1;
       const int32_t* col = cols + a.off_f[f];
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+      if constexpr (NCMAX >= 10) {
+        if (a.fam_rank[(int64_t)W * a.F + f] == 2) {  // two-row family
+          cd* R2 = B.r2 + (size_t)cta * B.kmax * 4 * T;
+          cof_pass2<NCMAX>(a, f, n, mem0, kW, wj, tid, T, B.kmax, col, arow, Dets,
+                           Ysm + (size_t)a.yoff[f] * T + tid, (pguard >> f) & 1, myStage, R2);
+          __syncwarp();
+          const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
+          const int nlive = rem < 32 ? (int)rem : 32;
+          const int mynsh = qtwo ? n - a.q_rank[(int64_t)Q * a.F + f] : 0;
+          scatter_rows2<NCMAX>(a, B, f, n, kW, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh, Stage, Ysm,
+                               R2, Dw + (size_t)f * B.slots_max * B.Lmax);
+          __syncwarp();
+          continue;
+        }
+      }
       const int64_t blk = ((int64_t)W * a.n_q + Q) * a.F + f;
       const bool twoc = B.kinv && qtwo && n >= 2 && a.q_rank[(int64_t)Q * a.F + f] == 1 && !a.kguard[blk];
       const int64_t wq = (int64_t)W * a.n_q + Q;

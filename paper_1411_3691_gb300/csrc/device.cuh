@@ -30,6 +30,7 @@ __device__ __forceinline__ cd cfms(cd a, cd b, cd acc) {
   return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
 }
 __device__ __forceinline__ cd cneg(cd a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ cd cadd(cd a, cd b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 // pivot measure |re| + |im| (one DADD; the absolute values are free operand modifiers)
 __device__ __forceinline__ double abs1(cd a) { return fabs(a.x) + fabs(a.y); }

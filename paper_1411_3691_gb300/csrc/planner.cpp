@@ -586,7 +586,7 @@ mhc_status build_plan(Plan& p) {
       }
     }
   }
-  // adjoint (rank-1 families only): the forward's block factors, solves and member dets
+  // adjoint: the forward's block factors, solves and member dets
   // again; per (family, sink, flavour) the aggregated row h and the shared-row cofactor
   // block -- from B^{-1} (computed once per two-sided block) for one-column sink families,
   // from the recomputed shared-row LU with the columns of A1^{-1} otherwise; per pair the
@@ -606,6 +606,20 @@ mhc_status build_plan(Plan& p) {
       one += inv + M * (8.0 * M + 6.0) + M * M * 14.0;                          // eta, beta, cofactor rows
       const double two = 8.0 * n - 2.0 + M * (22.0 * M + 6.0);                  // h.y, eta, cofactor rows
       const double scat = M * n * 2.0 + k * (n * 8.0 + 6.0 * std::max(F - 1, 0) + 1.0);
+      if (p.fam_rank[W * F + f] == 2) {
+        // two-row family: per member D = [b1; b2][z1 z2], det D, s, E, the member rows'
+        // coefficients; per sink the LU of A1 ((n-2) x (n-2)), the columns of A1^{-1}, the
+        // shared block rows; the scatter of 2k member rows and n-2 shared rows
+        const double M2 = n - 2;
+        double r2 = k * (64.0 * n + 6.0 * std::max(F - 1, 0) + 71.0);
+        r2 += flops_adjugate((int)M2);
+        for (int i = 0; i < (int)M2; i++)
+          r2 += 8.0 * (M2 - i - 1) * (M2 - i - 2) / 2.0 + 8.0 * M2 * (M2 - 1) / 2.0 + 6.0 * M2;
+        r2 += M2 * (38.0 * M2 + 18.0);
+        r2 += 2.0 * k * n * 16.0 + 2.0 * M2 * n;
+        bfl += (double)p.n_snk * r2;
+        continue;
+      }
       bfl += (double)p.n_snk * (gh + scat);
       if (p.fam_rank[W * F + f] == 1 && n >= 2) {
         bfl += (double)(one_sinks + qs2[f]) * one + (double)qs1[f] * two + (double)qc1[f] * inv;

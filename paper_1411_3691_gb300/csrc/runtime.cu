@@ -44,7 +44,7 @@ void free_device(DevicePlan& d) {
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
                   d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard, d.kinv, d.bwd_stage,
-                  d.bwd_accs};
+                  d.bwd_accs, d.bwd_r2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& bi : d.bwd_index) {
@@ -279,6 +279,11 @@ mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream) {
   if (c[0] & kStatusBadIndex) {
     set_error("a pair index was out of range");
     return MHC_EINVAL;
+  }
+  if (c[0] & kStatusUnsupported) {
+    set_error("the adjoint met a two-row family whose shared rows fail the pivot guard; its "
+              "gradient is left out: plan with opts.rank2 = 0");
+    return MHC_EUNSUPPORTED;
   }
   if (c[0] & kStatusNonFinite) {
     set_error("a non-finite value reached a result");

@@ -44,8 +44,10 @@ def gpu_backward(M, plan, S, g):
 def check_vs_oracle(M, w, opts=None):
     if opts is None:
         opts = M.default_opts()
-        opts.rank2 = 0 if w.name != "tc" else 1
+        opts.rank2 = 1 if w.name in ("tc", "r2") else 0
     plan = M.Plan.from_workload(w, opts)
+    if w.name == "r2":
+        assert plan.stats()["rank2_family_flavours"] > 0
     S = dev_S(w)
     ref = oracle.correlator_grad(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
     worst = 0.0
@@ -79,7 +81,21 @@ CASES = {
     "diagonal_S": lambda: _diag(),
     "repeated_labels": lambda: _repeat(),
     "two_column_sink_families": lambda: _two_col_sinks(),
+    "two_row_families": lambda: wl.make_workload("r2", [12, 10], [60, 48], [6, 5, 4, 7], [5, 6, 4, 3],
+                                                 seed=41, two_row_frac=0.5),
+    "two_row_sources_one_column_sinks": lambda: _two_row_sources(),
+    "two_row_families_n18": lambda: wl.make_workload("r2", [18, 18], [96, 96], [8, 6], [7, 5], diag=3.0,
+                                                     seed=43, two_row_frac=0.5),
 }
+
+
+def _two_row_sources():
+    """Two-row source families against sink families that change one column, so the
+    adjoint takes the two-sided rank-2 x rank-1 blocks (kapply2)."""
+    a = wl.make_workload("r2", [12, 10], [60, 48], [7, 5, 6], [9, 6, 8, 5], seed=47, two_row_frac=0.6)
+    b = wl.make_workload("r2", [12, 10], [60, 48], [7, 5, 6], [9, 6, 8, 5], seed=47, two_row_frac=0.0)
+    assert all(np.array_equal(x, y) for x, y in zip(a.S, b.S))
+    return wl.Workload("r2", a.n_f, a.S, a.labels_src, a.w_src, b.labels_snk, b.w_snk)
 
 
 def _two_col_sinks():
@@ -204,3 +220,25 @@ def test_full_helium4_fd_and_subplan(M):
     k = 8 * 16
     sub = wl.Workload("sub", w.n_f, w.S, w.labels_src[:k], w.w_src[:k], w.labels_snk, w.w_snk)
     check_vs_oracle(M, sub)
+
+
+def test_two_row_guard_is_reported(M):
+    """A two-row family whose shared rows hold a repeated label fails the pivot guard for
+    every sink: the adjoint leaves that block out and says so through the status
+    (MHC_EUNSUPPORTED), while the same input planned without two-row families is exact."""
+    w = CASES["two_row_families"]()
+    w.labels_src[:, 1] = w.labels_src[:, 0]          # rows 0 and 1 repeat in flavour 0
+    opts = M.default_opts()
+    opts.rank2 = 1
+    plan = M.Plan.from_workload(w, opts)
+    assert plan.stats()["rank2_family_flavours"] > 0
+    S = dev_S(w)
+    g = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
+    dS = [torch.empty_like(s) for s in S]
+    M.mhc_correlator_backward(plan.handle, S, g, None, None, dS, None, None)
+    with pytest.raises(M.MHCError) as e:
+        M.mhc_get_status(plan.handle)
+    assert e.value.status == M.MHC_EUNSUPPORTED
+    plan.close()
+    opts.rank2 = 0
+    check_vs_oracle(M, wl.Workload("rep", w.n_f, w.S, w.labels_src, w.w_src, w.labels_snk, w.w_snk), opts)
