@@ -225,7 +225,8 @@ def test_full_helium4_fd_and_subplan(M):
 def test_two_row_guard_is_reported(M):
     """A two-row family whose shared rows hold a repeated label fails the pivot guard for
     every sink: the adjoint leaves that block out and says so through the status
-    (MHC_EUNSUPPORTED), while the same input planned without two-row families is exact."""
+    (MHC_EUNSUPPORTED).  (Repeated labels under one-row families are exact: the
+    repeated_labels case.)"""
     w = CASES["two_row_families"]()
     w.labels_src[:, 1] = w.labels_src[:, 0]          # rows 0 and 1 repeat in flavour 0
     opts = M.default_opts()
@@ -240,5 +241,3 @@ def test_two_row_guard_is_reported(M):
         M.mhc_get_status(plan.handle)
     assert e.value.status == M.MHC_EUNSUPPORTED
     plan.close()
-    opts.rank2 = 0
-    check_vs_oracle(M, wl.Workload("rep", w.n_f, w.S, w.labels_src, w.w_src, w.labels_snk, w.w_snk), opts)

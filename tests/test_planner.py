@@ -241,6 +241,10 @@ def test_adjoint_flop_count_two_sided(M):
     assert two["two_sided_blocks"] > 0 and one["two_sided_blocks"] == 0
     assert two["backward_flops_per_call"] > two["flops_per_call"]
     assert one["backward_flops_per_call"] > one["flops_per_call"]
+    r2 = M.Plan.from_workload(wl.make_workload("r2", [12, 10], [60, 48], [6, 5, 4, 7], [5, 6, 4, 3],
+                                               seed=41, two_row_frac=0.5)).stats()
+    assert r2["rank2_family_flavours"] > 0
+    assert r2["backward_flops_per_call"] > 2 * r2["flops_per_call"]
     d_fwd = one["flops_per_call"] - two["flops_per_call"]
     d_bwd = one["backward_flops_per_call"] - two["backward_flops_per_call"]
     assert d_bwd > d_fwd > 0
