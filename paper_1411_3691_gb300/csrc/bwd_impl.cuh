@@ -322,11 +322,7 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
   for (int q = 0; q < n; q++) h[q] = make_double2(0.0, 0.0);
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
-    double wc = a.w_src[a.mem_term[m]] * wj;
-    if (__popc(a.mem_par[m]) & 1) wc = -wc;
-    cd g = make_double2(wc, 0.0);
-    for (int f2 = 0; f2 < a.F; f2++)
-      if (f2 != f) g = dev::cmul(g, Dets[dix(c, f2, B.kmax, T, tid)]);
+    const cd g = Dets[dix(c, f, B.kmax, T, tid)];  // gamma_c of this flavour
     const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
 #pragma unroll UNR
     for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
@@ -374,11 +370,7 @@ __device__ __noinline__ void cof_pass2(const FwdArgs& a, int f, int n, int mem0,
   cd s = make_double2(0.0, 0.0);
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
-    double wc = a.w_src[a.mem_term[m]] * wj;
-    if (__popc(a.mem_par[m]) & 1) wc = -wc;
-    cd g = make_double2(wc, 0.0);
-    for (int f2 = 0; f2 < a.F; f2++)
-      if (f2 != f) g = dev::cmul(g, Dets[dix(c, f2, kmax, T, tid)]);
+    const cd g = Dets[dix(c, f, kmax, T, tid)];  // gamma_c of this flavour
     const cd* r1 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
     const cd* r2 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2 + 1] * L;
     cd d00 = make_double2(0.0, 0.0), d01 = d00, d10 = d00, d11 = d00;
@@ -615,9 +607,6 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
     const bool act = s < nslots;
     const bool mem = s >= M;
     const int c = act && mem ? s - M : 0;
-    const int m = mem0 + c;
-    double wc = a.w_src[a.mem_term[m]];
-    if (__popc(a.mem_par[m]) & 1) wc = -wc;
     cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
     cd acc[NC];
     int curlab[NC];
@@ -632,7 +621,6 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
       const int src = jl & 31;
       const int Qj = __shfl_sync(FULL, myQ, src);
       const int nsj = __shfl_sync(FULL, mynsh, src);
-      const double wj = __shfl_sync(FULL, mywj, src);
       int cj[NC];
 #pragma unroll UNR
       for (int q = 0; q < n; q++) cj[q] = __shfl_sync(FULL, cl[q], src);
@@ -656,12 +644,7 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
         }
       }
       const int ts = warp * 32 + jl;
-      cd g = make_double2(1.0, 0.0);
-      if (mem) {
-        g = make_double2(wc * wj, 0.0);
-        for (int f2 = 0; f2 < a.F; f2++)
-          if (f2 != f) g = dev::cmul(g, Dets[dix(c, f2, B.kmax, T, ts)]);
-      }
+      const cd g = mem ? Dets[dix(c, f, B.kmax, T, ts)] : make_double2(1.0, 0.0);
       const cd* st = Stage + (size_t)ts * B.mn_max + (mem ? 0 : s * n);
 #pragma unroll UNR
       for (int q = 0; q < n; q++) {
@@ -793,6 +776,23 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       cd& s = AccS[c * T + tid];
       s.x = fma(wj, prod.x, s.x);
       s.y = fma(wj, prod.y, s.y);
+      // gamma_{c,f} = w_c w_j sign prod_{f' != f} det_{f'}, the weight of member c's
+      // cofactors in flavour f; it replaces the member's dets, which are not read again
+      const double wcj = wc * wj;
+      if (a.F == 2) {
+        const cd d0 = Dets[dix(c, 0, B.kmax, T, tid)], d1 = Dets[dix(c, 1, B.kmax, T, tid)];
+        Dets[dix(c, 0, B.kmax, T, tid)] = make_double2(wcj * d1.x, wcj * d1.y);
+        Dets[dix(c, 1, B.kmax, T, tid)] = make_double2(wcj * d0.x, wcj * d0.y);
+      } else {
+        cd dd[MHC_FMAX];
+        for (int f = 0; f < a.F; f++) dd[f] = Dets[dix(c, f, B.kmax, T, tid)];
+        for (int f = 0; f < a.F; f++) {
+          cd g = make_double2(wcj, 0.0);
+          for (int f2 = 0; f2 < a.F; f2++)
+            if (f2 != f) g = dev::cmul(g, dd[f2]);
+          Dets[dix(c, f, B.kmax, T, tid)] = g;
+        }
+      }
     }
     if (jpar) accj = dev::cneg(accj);  // back to the sink's own column order
     if (valid) B.dwsnk_part[(int64_t)W * a.n_snk + jo] = accj;

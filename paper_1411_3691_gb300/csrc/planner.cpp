@@ -605,7 +605,7 @@ mhc_status build_plan(Plan& p) {
         inv += 8.0 * (M - i - 1) * (M - i - 2) / 2.0 + 8.0 * M * (M - 1) / 2.0 + 6.0 * M;
       one += inv + M * (8.0 * M + 6.0) + M * M * 14.0;                          // eta, beta, cofactor rows
       const double two = 8.0 * n - 2.0 + M * (22.0 * M + 6.0);                  // h.y, eta, cofactor rows
-      const double scat = M * n * 2.0 + k * (n * 8.0 + 6.0 * std::max(F - 1, 0) + 1.0);
+      const double scat = M * n * 2.0 + k * n * 8.0;  // the members' gamma comes with h (gh)
       if (p.fam_rank[W * F + f] == 2) {
         // two-row family: per member D = [b1; b2][z1 z2], det D, s, E, the member rows'
         // coefficients; per sink the LU of A1 ((n-2) x (n-2)), the columns of A1^{-1}, the
