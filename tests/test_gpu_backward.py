@@ -84,6 +84,10 @@ CASES = {
     "two_row_families": lambda: wl.make_workload("r2", [12, 10], [60, 48], [6, 5, 4, 7], [5, 6, 4, 3],
                                                  seed=41, two_row_frac=0.5),
     "two_row_sources_one_column_sinks": lambda: _two_row_sources(),
+    "eight_flavours": lambda: wl.make_workload("f8", [2, 3, 1, 4, 2, 3, 1, 2], [12, 16, 8, 20, 12, 16, 8, 12],
+                                               [5, 4], [6, 3], seed=51),
+    "n32": lambda: wl.make_workload("n32", [32], [64], [3, 2], [6, 4], seed=12),
+    "single_terms": lambda: wl.make_workload("one", [3, 2], [10, 8], [1], [1], seed=53),
     "two_row_families_n18": lambda: wl.make_workload("r2", [18, 18], [96, 96], [8, 6], [7, 5], diag=3.0,
                                                      seed=43, two_row_frac=0.5),
 }
@@ -241,3 +245,11 @@ def test_two_row_guard_is_reported(M):
         M.mhc_get_status(plan.handle)
     assert e.value.status == M.MHC_EUNSUPPORTED
     plan.close()
+
+
+def test_backward_families_of_64(M):
+    w = wl.make_workload("fam64", [4, 4], [40, 40], [64, 10], [64, 5], seed=52)
+    opts = M.default_opts()
+    opts.max_family = 64
+    opts.rank2 = 0
+    check_vs_oracle(M, w, opts)

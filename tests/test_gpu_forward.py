@@ -65,6 +65,9 @@ def small_cases():
         "n32": wl.make_workload("n32", [32], [64], [3, 2], [40], seed=12),
         "two_rows_both_sides": wl.make_workload("tworow", [12, 10], [60, 48], [9, 7, 5], [8, 6, 7, 5, 30],
                                                 seed=23, two_row_frac=0.5),
+        "eight_flavours": wl.make_workload("f8", [2, 3, 1, 4, 2, 3, 1, 2], [12, 16, 8, 20, 12, 16, 8, 12],
+                                           [5, 4], [6, 3], seed=51),
+        "single_terms": wl.make_workload("one", [3, 2], [10, 8], [1], [1], seed=53),
     }
 
 
@@ -186,3 +189,15 @@ def test_full_large_nucleus_sampled(M):
     ref, scale = oracle.correlator(sub.S, sub.n_f, sub.labels_src, sub.w_src, sub.labels_snk, sub.w_snk,
                                    threads=16)
     assert abs(C - ref) <= 1e-11 * scale, (C, ref)
+
+
+def test_families_of_64(M):
+    """The largest family the planner forms (opts.max_family = 64) on both sides."""
+    w = wl.make_workload("fam64", [4, 4], [40, 40], [64, 10], [64, 5], seed=52)
+    opts = M.default_opts()
+    opts.max_family = 64
+    C, plan, S = gpu_C(M, w, opts)
+    assert plan.stats()["families"] == 2
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
