@@ -254,7 +254,8 @@ mhc_status mhc_pair_dets(mhc_plan_t plan, const double* const* S_f, int64_t n_pa
 
 /*
  * Wait for the stream, read the plan's device status word and counters, clear them.
- * Returns MHC_OK, MHC_ENONFINITE, MHC_EINVAL (bad pair index) or MHC_ETIMEOUT.
+ * Returns MHC_OK, MHC_ENONFINITE, MHC_EINVAL (bad pair index), MHC_ETIMEOUT, or
+ * MHC_EUNSUPPORTED (the adjoint left out a two-row family that failed the pivot guard).
  */
 mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream);
 
@@ -263,7 +264,10 @@ mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream);
  * counts) in one persistent launch, captured once into a CUDA graph.
  * mhc_batch_create autotunes the launch shape on the current device (it runs the
  * kernels on scratch inputs and synchronises) and uploads the plans.
- *   plans : host array of `count` plans; they must outlive the batch
+ *   plans : host array of `count` plans; they must outlive the batch.  A plan may appear
+ *           more than once: one plan evaluated on several propagator sets (gauge
+ *           configurations, time slices) in one launch, as the paper amortises the plan
+ *           (Sec. 3); its later entries get their own block-factor buffers.
  */
 mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* plans);
 void mhc_batch_destroy(mhc_batch_t batch);

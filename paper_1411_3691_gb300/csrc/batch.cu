@@ -110,6 +110,9 @@ struct mhc_batch_s {
   int64_t* d_nfam = nullptr;      // [count] families per plan
   int64_t k_total = 0;
   int k_big = 0;                  // a two-sided plan has a flavour with n > 6
+  // a plan given more than once (one plan, several propagator sets: gauge configurations,
+  // time slices) gets batch-owned block factors and guard flags for its later entries
+  std::vector<void*> own_kbuf, own_kguard;  // [count], null where the plan's own are used
   cudaStream_t side = nullptr;    // second branch: the class kernels run concurrently
   cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<const void*> key;  // S and out pointers the graph was captured with
@@ -184,10 +187,28 @@ size_t max_smem(const BatchShape& sh) {
 mhc_status fill_descs(mhc_batch_s& b, const BatchShape& sh, const double* const* const* S,
                       std::vector<FwdArgs>& desc) {
   desc.resize(b.count);
+  b.own_kbuf.resize(b.count, nullptr);
+  b.own_kguard.resize(b.count, nullptr);
   for (int k = 0; k < b.count; k++) {
+    const Plan& p = *b.plans[k];
     mhc_status st = fill_fwd_args(*b.plans[k], S[k], nullptr, nullptr, desc[k]);
     if (st != MHC_OK) return st;
     desc[k].n_tiles = sh.n_tiles[k];
+    bool repeat = false;
+    for (int k2 = 0; k2 < k; k2++) repeat |= b.plans[k2] == b.plans[k];
+    if (repeat && desc[k].snk_orig) {
+      if (!b.own_kbuf[k]) {
+        const size_t nk = (size_t)p.n_fam * p.n_qfam * desc[k].kstride * sizeof(double2);
+        const size_t ng = (size_t)p.n_fam * p.n_qfam * p.F * sizeof(int32_t);
+        if (cudaMalloc(&b.own_kbuf[k], std::max<size_t>(nk, 16)) != cudaSuccess ||
+            cudaMalloc(&b.own_kguard[k], std::max<size_t>(ng, 16)) != cudaSuccess) {
+          set_error("mhc_batch: cudaMalloc failed for a repeated plan's block factors");
+          return MHC_ENOMEM;
+        }
+      }
+      desc[k].kbuf = reinterpret_cast<const double2*>(b.own_kbuf[k]);
+      desc[k].kguard = reinterpret_cast<int32_t*>(b.own_kguard[k]);
+    }
   }
   return MHC_OK;
 }
@@ -277,6 +298,10 @@ void destroy(mhc_batch_s* b) {
   void* ptrs[] = {b->d_desc, b->d_items, b->d_part_off, b->d_partials, b->d_head, b->d_outs,
                   b->d_kpref, b->d_nfam};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : b->own_kbuf)
+    if (p) cudaFree(p);
+  for (void* p : b->own_kguard)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->side) cudaStreamDestroy(b->side);

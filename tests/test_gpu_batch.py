@@ -100,3 +100,26 @@ def test_full_batch_64_correlators(M):
     M.mhc_batch_destroy(batch)
     for p in plans:
         p.close()
+
+
+def test_one_plan_many_configurations(M):
+    """One plan given four times with four propagator sets (gauge configurations): every
+    entry matches its own mhc_correlator call and the oracle."""
+    w = wl.helium4(scale=6 / 256)
+    plan = M.Plan.from_workload(w)
+    rng = np.random.default_rng(99)
+    sets = [[wl.make_S(rng, s.shape[0], 2.0) for s in w.S] for _ in range(4)]
+    S = [[torch.from_numpy(np.ascontiguousarray(s)).cuda() for s in Sk] for Sk in sets]
+    batch = M.mhc_batch_create([plan.handle] * 4)
+    outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in range(4)]
+    M.mhc_batch_correlator(batch, S, outs)
+    torch.cuda.synchronize()
+    got = [complex(*o.cpu().numpy()) for o in outs]
+    for k in range(4):
+        ref, scale = oracle.correlator(sets[k], w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+        assert abs(got[k] - ref) <= 1e-11 * scale, (k, got[k], ref)
+        plain = complex(*plan.correlator(S[k]).cpu().numpy())
+        assert abs(got[k] - plain) <= 1e-11 * scale
+    assert len({round(g.real, 6) for g in got}) == 4      # four different configurations
+    M.mhc_get_status(plan.handle)
+    M.mhc_batch_destroy(batch)
