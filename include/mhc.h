@@ -194,6 +194,19 @@ mhc_status mhc_correlator(mhc_plan_t plan, const double* const* S_f, const doubl
                           const double* w_snk_dev, double* out_dev, mhc_stream_t stream);
 
 /*
+ * Forward correlator with complex weights w_i = w_src_re[i] + i w_src_im[i] and
+ * w_j = w_snk_re[j] + i w_snk_im[j] (all four device float64 arrays, required), for
+ * wavefunctions with complex coefficients.  The sum is bilinear in the weights, so
+ *   C = C(re, re) - C(im, im) + i (C(re, im) + C(im, re))
+ * with C(x, y) the real-weight correlator of mhc_correlator (Sec. 1); the block factors
+ * are computed once for the four passes and the combination runs on the device.
+ * out_dev: device float64 [2], (Re C, Im C).  Not a separate method in the paper.
+ */
+mhc_status mhc_correlator_cw(mhc_plan_t plan, const double* const* S_f, const double* w_src_re,
+                             const double* w_src_im, const double* w_snk_re, const double* w_snk_im,
+                             double* out_dev, mhc_stream_t stream);
+
+/*
  * Adjoint (hand-written; Jacobi's formula d det G / dG = cofactor matrix, with the LU
  * factors recomputed).  With g = g_out[0] + i g_out[1] = dL/dRe C + i dL/dIm C and the
  * holomorphic derivatives D_S = dC/dS_f, D_w = dC/dw:

@@ -31,6 +31,16 @@ __global__ void __launch_bounds__(1024) reduce_kernel(const double2* __restrict_
 
 }  // namespace
 
+// Complex weights by bilinearity: with w_i = a_i + i b_i and w_j = c_j + i d_j,
+// C = C(a, c) - C(b, d) + i (C(a, d) + C(b, c)), each C(x, y) a real-weight correlator.
+// t holds C(a, c), C(a, d), C(b, c), C(b, d) as (Re, Im) pairs.
+__global__ void combine_cw(const double* __restrict__ t, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    out[0] = t[0] - t[6] - (t[3] + t[5]);
+    out[1] = t[1] - t[7] + (t[2] + t[4]);
+  }
+}
+
 size_t forward_smem_bytes(int slots, int tile) {
   const size_t cache = (size_t)slots * tile * sizeof(double2);
   const size_t queue = (size_t)(tile / 32) * kQueueCap * kQueueEntryBytes;
@@ -57,6 +67,28 @@ cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam,
     e = launch_fwd_nc32(a, tile, items, smem, s);
   if (e != cudaSuccess) return e;
   return launch_reduce(a.partials, items, out, s);
+}
+
+cudaError_t launch_forward_cw(const FwdArgs& a0, const double* const* ws, const double* const* wk,
+                              int ncmax, int tile, int64_t n_fam, int64_t items, size_t smem, double* tmp,
+                              double* out, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (a0.snk_orig) {  // the block factors do not depend on the weights: once for the four passes
+    e = ncmax <= 8 ? launch_kfac_nc8(a0, n_fam, s)
+                   : (ncmax <= 18 ? launch_kfac_nc18(a0, n_fam, s) : launch_kfac_nc32(a0, n_fam, s));
+    if (e != cudaSuccess) return e;
+  }
+  for (int k = 0; k < 4; k++) {
+    FwdArgs a = a0;
+    a.w_src = ws[k >> 1];
+    a.w_snk = wk[k & 1];
+    e = ncmax <= 8 ? launch_fwd_nc8(a, tile, items, smem, s)
+                   : (ncmax <= 18 ? launch_fwd_nc18(a, tile, items, smem, s) : launch_fwd_nc32(a, tile, items, smem, s));
+    if (e != cudaSuccess) return e;
+    if ((e = launch_reduce(a.partials, items, tmp + 2 * k, s)) != cudaSuccess) return e;
+  }
+  combine_cw<<<1, 32, 0, s>>>(tmp, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double2* partials, int64_t items, double* out, cudaStream_t s) {

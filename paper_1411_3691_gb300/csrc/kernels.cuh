@@ -236,6 +236,9 @@ constexpr int kQueueEntryBytes = 48;  // sizeof(fwd::QEntry)
 cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,
                            size_t smem, double* out, cudaStream_t s);
 cudaError_t launch_reduce(const double2* partials, int64_t items, double* out, cudaStream_t s);
+cudaError_t launch_forward_cw(const FwdArgs& a0, const double* const* ws, const double* const* wk,
+                              int ncmax, int tile, int64_t n_fam, int64_t items, size_t smem, double* tmp,
+                              double* out, cudaStream_t s);
 cudaError_t launch_pairs(const FwdArgs& a, int ncmax, int64_t n_pairs, int64_t n_src,
                          const int64_t* ii, const int64_t* jj, const int32_t* src_member,
                          const int32_t* mem_family, double* dets, int32_t* path, cudaStream_t s);

@@ -44,7 +44,7 @@ void free_device(DevicePlan& d) {
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
                   d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard, d.kinv, d.bwd_stage,
-                  d.bwd_accs, d.bwd_r2};
+                  d.bwd_accs, d.bwd_r2, d.cw_tmp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& bi : d.bwd_index) {
@@ -237,6 +237,31 @@ mhc_status mhc_correlator(mhc_plan_t plan, const double* const* S_f, const doubl
   const size_t smem = forward_smem_bytes(a.slots, tile);
   MHC_CUDA(launch_forward(a, plan_ncmax(p), tile, p.n_fam, p.dev.n_items, smem, out_dev,
                           reinterpret_cast<cudaStream_t>(stream)));
+  return MHC_OK;
+}
+
+mhc_status mhc_correlator_cw(mhc_plan_t plan, const double* const* S_f, const double* w_src_re,
+                             const double* w_src_im, const double* w_snk_re, const double* w_snk_im,
+                             double* out_dev, mhc_stream_t stream) {
+  if (!plan || !out_dev || !w_src_re || !w_src_im || !w_snk_re || !w_snk_im) {
+    set_error("mhc_correlator_cw: NULL plan, weight or output");
+    return MHC_EINVAL;
+  }
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  mhc_status st = ensure_device(p);
+  if (st != MHC_OK) return st;
+  if (!p.dev.cw_tmp && cudaMalloc(&p.dev.cw_tmp, 8 * sizeof(double)) != cudaSuccess) {
+    set_error("mhc_correlator_cw: cudaMalloc failed");
+    return MHC_ENOMEM;
+  }
+  FwdArgs a;
+  if ((st = fill_fwd_args(p, S_f, w_src_re, w_snk_re, a)) != MHC_OK) return st;
+  const double* ws[2] = {w_src_re, w_src_im};
+  const double* wk[2] = {w_snk_re, w_snk_im};
+  const int tile = p.dev.tile;
+  const size_t smem = forward_smem_bytes(a.slots, tile);
+  MHC_CUDA(launch_forward_cw(a, ws, wk, plan_ncmax(p), tile, p.n_fam, p.dev.n_items, smem, p.dev.cw_tmp,
+                             out_dev, reinterpret_cast<cudaStream_t>(stream)));
   return MHC_OK;
 }
 

@@ -27,6 +27,7 @@ MHC_FMAX = 8
 
 EXPORTED = ["mhc_last_error", "mhc_plan_opts_default", "mhc_plan", "mhc_plan_destroy",
             "mhc_plan_stats", "mhc_plan_families", "mhc_plan_sinks", "mhc_correlator", "mhc_correlator_noalloc",
+            "mhc_correlator_cw",
             "mhc_correlator_backward",
             "mhc_pair_dets", "mhc_get_status", "mhc_batch_create", "mhc_batch_destroy",
             "mhc_batch_correlator", "mhc_batch_info", "mhc_fp64_peak"]
@@ -212,6 +213,18 @@ def mhc_correlator(plan, S, w_src=None, w_snk=None, out=None, stream=None):
     if out is None:
         out = torch.empty(2, dtype=torch.float64, device=S[0].device)
     _check(lib().mhc_correlator(_vp(plan), _S_ptrs(S), _ptr(w_src), _ptr(w_snk), _ptr(out), _stream(stream)))
+    return out
+
+
+def mhc_correlator_cw(plan, S, w_src, w_snk, out=None, stream=None):
+    """Forward correlator with complex weights: w_src, w_snk complex128 CUDA tensors (their
+    real and imaginary parts are passed as separate float64 arrays).  Returns out."""
+    import torch
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=S[0].device)
+    parts = [torch.view_as_real(w)[:, k].contiguous() for w in (w_src, w_snk) for k in (0, 1)]
+    _check(lib().mhc_correlator_cw(_vp(plan), _S_ptrs(S), _ptr(parts[0]), _ptr(parts[1]), _ptr(parts[2]),
+                                   _ptr(parts[3]), _ptr(out), _stream(stream)))
     return out
 
 

@@ -201,3 +201,26 @@ def test_families_of_64(M):
     ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
     assert abs(C - ref) <= 1e-11 * scale, (C, ref)
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+
+
+def test_complex_weights(M):
+    """mhc_correlator_cw against the oracle through bilinearity: four real-weight oracle
+    sums combined as C = C(a, c) - C(b, d) + i (C(a, d) + C(b, c))."""
+    w = CASES["two_rows_both_sides"]
+    plan = M.Plan.from_workload(w)
+    S = dev_S(w)
+    rng = np.random.default_rng(17)
+    a, b = rng.normal(size=len(w.w_src)), rng.normal(size=len(w.w_src))
+    c, d = rng.normal(size=len(w.w_snk)), rng.normal(size=len(w.w_snk))
+    ws = torch.from_numpy(a + 1j * b).cuda()
+    wk = torch.from_numpy(c + 1j * d).cuda()
+    out = M.mhc_correlator_cw(plan.handle, S, ws, wk)
+    got = complex(*out.cpu().numpy())
+    parts, scale = {}, 0.0
+    for kx, x in (("a", a), ("b", b)):
+        for ky, y in (("c", c), ("d", d)):
+            parts[kx + ky], sc = oracle.correlator(w.S, w.n_f, w.labels_src, x, w.labels_snk, y, threads=8)
+            scale += sc
+    ref = parts["ac"] - parts["bd"] + 1j * (parts["ad"] + parts["bc"])
+    assert abs(got - ref) <= 1e-11 * scale, (got, ref)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
