@@ -23,10 +23,10 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
 namespace {
 
 // dS_f[a][b] = g conj(sum over (W, slot) rows labelled a, chunks, warps of the partials).
-// One block per (row a, group of 32 columns): lane = column, the 8 warps take the terms
+// One block per (row a, group of 32 columns): lane = column, the 32 warps take the terms
 // (row entry, chunk, warp) round-robin in a fixed order, then a fixed-order sum over the
 // warps -- the same result on every call.
-constexpr int kFinWarps = 8;
+constexpr int kFinWarps = 32;
 __global__ void __launch_bounds__(32 * kFinWarps)
     fin_dS_kernel(int f, int L, const int32_t* __restrict__ list_off, const int2* __restrict__ list,
                   const double2* __restrict__ part, int n_chunks, int warps, int F, int slots_max,
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32 * kFinWarps)
   const int64_t per = (int64_t)n_chunks * warps;
   const int nk = list_off[a + 1] - k0;
   double2 s = make_double2(0.0, 0.0);
-  // term t = k * per + cw (cw = chunk * warps + warp); this warp takes t = wp, wp + 8, ...
+  // term t = k * per + cw (cw = chunk * warps + warp); this warp takes t = wp, wp + kFinWarps, ...
   int k = 0;
   int64_t cw = wp;
   while (cw >= per) {
