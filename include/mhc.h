@@ -55,7 +55,7 @@ typedef enum {
   MHC_ECUDA = 3,        /* a CUDA runtime call failed                            */
   MHC_ETIMEOUT = 4,     /* a bounded device wait ran out                         */
   MHC_ENONFINITE = 5,   /* a non-finite value reached a result (NaN/Inf input)   */
-  MHC_EUNSUPPORTED = 6  /* valid request that this build does not implement      */
+  MHC_EUNSUPPORTED = 6  /* valid request that the library does not implement    */
 } mhc_status;
 
 #define MHC_NMAX 32     /* largest n_f (quarks of one flavour in a term) */
@@ -91,7 +91,8 @@ typedef struct {
   int64_t members;               /* == n_src                                          */
   int64_t graph_edges;           /* edges of the source-term graph                    */
   double flops_per_call;         /* algorithmic FP64 flops of one mhc_correlator call,
-                                    without refactors (counting rule in the design doc)     */
+                                    without refactors (real add/mul 1, FMA 2, complex
+                                    multiply 6, complex FMA 8, complex reciprocal 6)  */
   double fresh_lu_flops_per_pair;/* flops of one refactored pair (all flavours)        */
   double bytes_per_call;         /* algorithmic bytes: S_f once, labels, weights, out */
   double plan_seconds;           /* host time spent in mhc_plan                       */
