@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(128) kfac_batch_kernel(const FwdArgs* __restri
 // dev::group_lu).  One warp per thread block; GPW blocks per warp.
 template <int NCMAX>
 struct KGroup {
-  static constexpr int G = NCMAX <= 18 ? 4 : 16;              // lanes per block
+  static constexpr int G = NCMAX <= 8 ? 4 : (NCMAX <= 18 ? 8 : 16);  // lanes per block
   static constexpr int GPW = 32 / G;                           // blocks per warp
   // complex per block (matrix + back-substitution vector), padded to 4 mod 8 16-byte units
   // so that two groups sharing an 8-lane shared-memory phase use disjoint bank groups
