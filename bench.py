@@ -346,7 +346,9 @@ def time_adjoint(mhc, plan, S, flush, stream, fwd_ms, pairs, steps=5):
     return {"ms_per_step": ms, "ratio_vs_forward": ms / fwd_ms, "pairs_per_s": pairs / (ms * 1e-3),
             "tflops": bflops / (ms * 1e-3) / 1e12, "flops_per_step": bflops,
             "outputs": "dS_f (2 x 48 x 48 complex), dw_src [4096], dw_snk [4096]; L = Re C",
-            "gpu_launches_per_step": 6 if plan.stats()["two_sided_blocks"] > 0 else 5}
+            # block factors and B^-1 (two-sided plans), the adjoint kernel, one dS finalize per
+            # flavour, the two weight finalizes
+            "gpu_launches_per_step": (3 if plan.stats()["two_sided_blocks"] > 0 else 1) + len(S) + 2}
 
 
 def time_batch(mhc, flush, stream, count=64, reps=3):

@@ -208,8 +208,9 @@ mhc_status mhc_correlator_cw(mhc_plan_t plan, const double* const* S_f, const do
                              double* out_dev, mhc_stream_t stream);
 
 /*
- * Adjoint (hand-written; Jacobi's formula d det G / dG = cofactor matrix, with the LU
- * factors recomputed).  With g = g_out[0] + i g_out[1] = dL/dRe C + i dL/dIm C and the
+ * Adjoint (hand-written; Jacobi's formula d det G / dG = cofactor matrix: the member
+ * rows' cofactors are the forward's cached solves, the shared rows' come from B^{-1} of
+ * each two-sided block or from the recomputed shared-row LU, never dividing by det G).  With g = g_out[0] + i g_out[1] = dL/dRe C + i dL/dIm C and the
  * holomorphic derivatives D_S = dC/dS_f, D_w = dC/dw:
  *   dS_f[a][b] = g * conj(D_S[a][b])      (complex128 L_f x L_f, device, written)
  *   dw_src[i]  = Re(conj(g) * D_w_src[i]) (float64, device, written)

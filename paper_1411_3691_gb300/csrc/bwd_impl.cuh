@@ -593,7 +593,7 @@ template <int NC, int NFIX>
 __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B, int f, int n_rt,
                                              int kW, int mem0, int nlive, int T, int warp, int lane,
                                              const int32_t* __restrict__ mycol, int myQ, int mynsh,
-                                             double mywj, const cd* Stage, const cd* Ysm,
+                                             const cd* Stage, const cd* Ysm,
                                              const cd* Dets, cd* Df) {
   constexpr int UNR = NFIX ? NC : 1;
   constexpr unsigned FULL = 0xffffffffu;
@@ -663,10 +663,10 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
 template <int NCMAX>
 __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs& B, int f, int n,
                                                  int kW, int mem0, int nlive, int T, int warp, int lane,
-                                                 const int32_t* mycol, int myQ, int mynsh, double mywj,
+                                                 const int32_t* mycol, int myQ, int mynsh,
                                                  const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
 #define MHC_SC(NN) scatter_rows<NN, NN>(a, B, f, NN, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, \
-                                        mywj, Stage, Ysm, Dets, Df)
+                                        Stage, Ysm, Dets, Df)
   switch (n) {
     case 1: MHC_SC(1); return;
     case 2: MHC_SC(2); return;
@@ -675,8 +675,8 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
     case 5: MHC_SC(5); return;
     case 6: MHC_SC(6); return;
     default:
-      scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, mywj, Stage,
-                             Ysm, Dets, Df);
+      scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, Stage, Ysm,
+                             Dets, Df);
   }
 #undef MHC_SC
 }
@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
       const int nlive = rem < 32 ? (int)rem : 32;
       dispatch_scatter<NCMAX>(a, B, f, n, kW, mem0, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh,
-                              wj, Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax);
+                              Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax);
       __syncwarp();
     }
   }
