@@ -75,7 +75,7 @@ typedef struct {
   int32_t max_family;  /* largest number of members per family, 1..64.          32    */
   int32_t one_sided;   /* 1: only source-side families (Sec. 3 as printed); 0: sink
                           terms are grouped too, and each (source family, sink
-                          family) block shares adj(B) of its common rows and
+                          family) block shares the LU factors of its common rows and
                           columns (two-sided update).                           0     */
   int32_t reserved[7];
 } mhc_plan_opts;
@@ -175,7 +175,7 @@ mhc_status mhc_plan_families(mhc_plan_t plan, int64_t* n_families, int64_t* fam_
  *                     determinant in the original column order is (-1)^bit times the
  *                     determinant in the aligned order)
  *   family          : int32 [n_snk]; sink family of each position
- *   two_sided       : int32 [Q]; 1 when the family shares adj(B) (two or more sinks)
+ *   two_sided       : int32 [Q]; 1 when the family shares B's factors (two or more sinks)
  * With opts->one_sided every sink is its own family and the update is one-sided.
  */
 mhc_status mhc_plan_sinks(mhc_plan_t plan, int64_t* n_sink_families, int32_t* order,

@@ -50,7 +50,7 @@ size_t forward_smem_bytes(int slots, int tile) {
 cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,
                            size_t smem, double* out, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (a.snk_orig) {  // two-sided update: adj(B) of every (family, sink family) block first
+  if (a.snk_orig) {  // two-sided update: the LU factors of every (family, sink family) block first
     if (ncmax <= 8)
       e = launch_kfac_nc8(a, n_fam, s);
     else if (ncmax <= 18)

@@ -44,7 +44,7 @@ struct FwdArgs {
   const int32_t* q_two;      // [Q] 1: the family uses the two-sided update
   const int32_t* q_rank;     // [Q][F] changed columns (1 or 2) of the sink family
   const int32_t* q_off;      // [Q + 1] first position of each sink family
-  const double2* kbuf;       // [W][Q][kstride]: per flavour adj(B) row-major, then det(B)
+  const double2* kbuf;       // [W][Q][kstride]: per flavour the LU factors of B (see kapply)
   int32_t* kguard;           // [W][Q][F] 1: the block's pivot guard fired
   int64_t n_q;
   int kstride;

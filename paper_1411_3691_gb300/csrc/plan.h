@@ -39,7 +39,7 @@ struct DevicePlan {
   int32_t* q_off = nullptr;
   int32_t* q_two = nullptr;
   int32_t* q_rank = nullptr;
-  double* kbuf = nullptr;        // [W][Q][sum_f ((n_f-1)^2 + 1)] adj(B) and det(B)
+  double* kbuf = nullptr;        // [W][Q][kstride] LU factors of B, row order, -det B, det B
   int32_t* kguard = nullptr;     // [W][Q][F] 1: the block's pivot guard fired
   double* bwd_stage = nullptr;   // [cta][T][mn_max] adjoint staging
   size_t bwd_stage_bytes = 0;

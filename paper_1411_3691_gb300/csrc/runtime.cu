@@ -119,7 +119,7 @@ mhc_status ensure_device(Plan& p) {
   if ((st = upload(&d.mem_family, p.mem_family.data(), p.mem_family.size())) != MHC_OK) return st;
   if ((st = upload(&d.w_src, p.w_src.data(), p.w_src.size())) != MHC_OK) return st;
   if ((st = upload(&d.w_snk, p.w_snk.data(), p.w_snk.size())) != MHC_OK) return st;
-  // two-sided update: sink tables and the adj(B) store (skipped above 16 GB)
+  // two-sided update: sink tables and the block-factor store (skipped above 16 GB)
   size_t kstride = 0;
   for (int f = 0; f < p.F; f++) kstride += kblock_size(p.n_f[f]);
   const double kbytes = (double)p.n_fam * (double)p.n_qfam * (double)kstride * 16.0;

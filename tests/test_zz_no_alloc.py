@@ -24,9 +24,19 @@ def M():
     return mhc
 
 
-def test_noalloc_matches_correlator_twice(M):
-    w = wl.helium4(scale=8 / 256)
-    w.labels_snk, w.w_snk = w.labels_snk[:1000], w.w_snk[:1000]
+def _case(name):
+    if name == "he4":
+        w = wl.helium4(scale=8 / 256)
+        w.labels_snk, w.w_snk = w.labels_snk[:1000], w.w_snk[:1000]
+        return w
+    # n > 6 and two-row families: block factors by lane groups, rank-2 solves
+    return wl.make_workload("tworow", [12, 10], [60, 48], [9, 7, 5], [8, 6, 7, 5, 30], seed=23,
+                            two_row_frac=0.5)
+
+
+@pytest.mark.parametrize("name", ["he4", "two_rows_n12"])
+def test_noalloc_matches_correlator_twice(M, name):
+    w = _case(name)
     plan = M.Plan.from_workload(w)
     S = [torch.from_numpy(s).cuda() for s in w.S]
     ref = plan.correlator(S).cpu().numpy()            # ordinary entry point (uploads the plan)
