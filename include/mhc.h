@@ -60,6 +60,8 @@ typedef enum {
 
 #define MHC_NMAX 32     /* largest n_f (quarks of one flavour in a term) */
 #define MHC_FMAX 8      /* largest number of flavours */
+#define MHC_MAX_RANK 3  /* most changed rows per family and flavour (stride of the
+                           changed-row tables of mhc_plan_families) */
 
 /* Planner options.  mhc_plan_opts_default() fills the defaults listed here. */
 typedef struct {
@@ -77,7 +79,12 @@ typedef struct {
                           terms are grouped too, and each (source family, sink
                           family) block shares the LU factors of its common rows and
                           columns (two-sided update).                           0     */
-  int32_t reserved[7];
+  int32_t rank3;       /* 1 (with rank2): source families may also differ in three
+                          rows per flavour with n_f >= 14 (rank-3 update: a 3x3
+                          generalised cofactor with three null vectors; the
+                          general rank-k update of Sec. 5 taken to k = 3); the
+                          adjoint does not differentiate such plans.            0     */
+  int32_t reserved[6];
 } mhc_plan_opts;
 
 /* Planner and run statistics. */
@@ -102,7 +109,8 @@ typedef struct {
   int64_t sink_families;         /* sink-side families (two-sided update)             */
   int64_t two_sided_blocks;      /* (family, sink family, flavour) blocks sharing B's LU */
   double backward_flops_per_call;/* algorithmic FP64 flops of one mhc_correlator_backward */
-  int64_t reserved[3];
+  int64_t rank3_family_flavours; /* (family, flavour) blocks updated at rank 3        */
+  int64_t reserved[2];
 } mhc_stats;
 
 /* Thread-local message describing the last failure of this thread's last call. */
@@ -147,14 +155,14 @@ mhc_status mhc_plan_stats(mhc_plan_t plan, mhc_stats* out);
  * Export the work families (host; for inspection and tests).  Pass NULL for the
  * arrays to query the sizes only.  With W = *n_families and Tn = sum_f n_f:
  *   fam_member_offset : int64 [W+1]; members of family w are [off[w], off[w+1])
- *   fam_rank          : int32 [W][F]; 0 (n_f = 0), 1 or 2 changed rows
- *   fam_rows          : int32 [W][F][2]; changed-row positions in the reference tuple
+ *   fam_rank          : int32 [W][F]; 0 (n_f = 0), 1, 2 or 3 changed rows
+ *   fam_rows          : int32 [W][F][3]; changed-row positions in the reference tuple
  *                       (ascending; -1 when unused)
  *   fam_ref           : int32 [W][Tn]; the dominator's labels (reference tuple)
  *   member_term       : int64 [n_src]; source term of each member
  *   member_sign       : int32 [n_src]; +-1: det of the term's own label order equals
  *                       member_sign times prod_f det [shared rows; member rows]
- *   member_labels     : int32 [n_src][F][2]; the member's labels at the changed rows
+ *   member_labels     : int32 [n_src][F][3]; the member's labels at the changed rows
  * "[shared rows; member rows]" is the matrix whose rows are, in order, the reference
  * tuple's labels at the positions not in fam_rows (ascending), then the member's labels
  * at fam_rows (ascending), and whose columns are the sink term's labels.

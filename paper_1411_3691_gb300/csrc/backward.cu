@@ -133,7 +133,14 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   Plan& p = *reinterpret_cast<Plan*>(plan);
   bool any_r2 = false;  // two-row families: two member rows per member, coefficient scratch
   for (int64_t W = 0; W < p.n_fam; W++)
-    for (int f = 0; f < p.F; f++) any_r2 |= p.fam_rank[W * p.F + f] == 2;
+    for (int f = 0; f < p.F; f++) {
+      any_r2 |= p.fam_rank[W * p.F + f] == 2;
+      if (p.fam_rank[W * p.F + f] >= 3) {
+        set_error("mhc_correlator_backward: the adjoint of three-row families is not built; "
+                  "plan with opts.rank3 = 0");
+        return MHC_EUNSUPPORTED;
+      }
+    }
   mhc_status st = ensure_device(p);
   if (st != MHC_OK) return st;
   BwdArgs b;
@@ -202,7 +209,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
           for (int64_t c = 0; c < p.fam_off[W + 1] - p.fam_off[W]; c++) {
             const int64_t mm = p.fam_off[W] + c;
             for (int t = 0; t < rho; t++)
-              lists[p.mem_lab[(mm * F + f) * 2 + t]].push_back({(int)W, (int)(n - rho + rho * c + t)});
+              lists[p.mem_lab[(mm * F + f) * MHC_MAX_RANK + t]].push_back({(int)W, (int)(n - rho + rho * c + t)});
           }
         }
       }

@@ -323,7 +323,7 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
     const cd g = Dets[dix(c, f, B.kmax, T, tid)];  // gamma_c of this flavour
-    const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
+    const cd* brow = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK] * L;
 #pragma unroll UNR
     for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
   }
@@ -371,8 +371,8 @@ __device__ __noinline__ void cof_pass2(const FwdArgs& a, int f, int n, int mem0,
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
     const cd g = Dets[dix(c, f, kmax, T, tid)];  // gamma_c of this flavour
-    const cd* r1 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2] * L;
-    const cd* r2 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * 2 + 1] * L;
+    const cd* r1 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK] * L;
+    const cd* r2 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + 1] * L;
     cd d00 = make_double2(0.0, 0.0), d01 = d00, d10 = d00, d11 = d00;
     for (int q = 0; q < n; q++) {
       const cd b1 = dev::ldS(r1 + col[q]), b2 = dev::ldS(r2 + col[q]);
@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
           const int32_t* col = cols + a.off_f[f];
           const int rho = a.fam_rank[(int64_t)W * a.F + f];
           if (!fail)
-            d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
+            d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK,
                                             col, Ysm + (size_t)a.yoff[f] * T + tid, T, ey[f], a.kc, &fail);
           if (fail) {
             dev::member_rows(a, W, m, f, rho, rows);

@@ -164,14 +164,15 @@ __device__ __forceinline__ bool shared_rows(const cd* __restrict__ S, int L, int
         Y[(t * n + q) * ys] = z[q];
         ez = max(ez, expo(z[q]));
       }
-      Y[(t * n + M + t) * ys] = make_double2(1.0, 0.0);      // z_t = [.. ; e_t]
-      Y[(t * n + M + 1 - t) * ys] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < RHO; u++)  // z_t = [.. ; e_t]
+        Y[(t * n + M + u) * ys] = make_double2(u == t ? 1.0 : 0.0, 0.0);
     }
   }
-  if (RHO == 2) {
-    Y[(2 * n) * ys] = sd;
+  if (RHO >= 2) {
+    Y[(RHO * n) * ys] = sd;
     ez = max(ez, 0);  // the unit entries of z
-    *ey = expo(sd) + 2 * ez;
+    *ey = expo(sd) + RHO * ez;
   } else {
     *ey = ez;
   }
@@ -199,6 +200,35 @@ __device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_
       eb = max(eb, expo(b));
       d = cfma(b, Y[q * ys], d);
     }
+    *fail = expo(d) < eb + ey - kc;
+    return d;
+  } else if (RHO == 3) {
+    // sd det(B Z), B the three member rows, Z = [z1 z2 z3]: nine dots, a 3 x 3 det by
+    // cofactors of the first row
+    const cd* r[3] = {S + (size_t)lab[0] * L, S + (size_t)lab[1] * L, S + (size_t)lab[2] * L};
+    cd D[3][3];
+    int eb = 0;
+#pragma unroll
+    for (int u = 0; u < 3; u++)
+#pragma unroll
+      for (int v = 0; v < 3; v++) D[u][v] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < 3; u++) {
+      int e = -4096;
+#pragma unroll UNR
+      for (int q = 0; q < n; q++) {
+        const cd b = ldS(r[u] + colp[q]);
+        e = max(e, expo(b));
+#pragma unroll
+        for (int v = 0; v < 3; v++) D[u][v] = cfma(b, Y[(v * n + q) * ys], D[u][v]);
+      }
+      eb += e;
+    }
+    const cd m0 = cfms(D[1][2], D[2][1], cmul(D[1][1], D[2][2]));
+    const cd m1 = cfms(D[1][2], D[2][0], cmul(D[1][0], D[2][2]));
+    const cd m2 = cfms(D[1][1], D[2][0], cmul(D[1][0], D[2][1]));
+    const cd dd = cfma(D[0][2], m2, cfms(D[0][1], m1, cmul(D[0][0], m0)));
+    const cd d = cmul(Y[3 * n * ys], dd);
     *fail = expo(d) < eb + ey - kc;
     return d;
   } else {

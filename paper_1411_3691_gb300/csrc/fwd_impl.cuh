@@ -47,7 +47,7 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
   const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   // lane i < n: row i of the n x (n - 1) block (rows: shared rows, then the member's row)
-  const int rlab = lane < n - 1 ? arow[lane] : a.mem_lab[((int64_t)m * a.F + f) * 2];
+  const int rlab = lane < n - 1 ? arow[lane] : a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK];
   dev::cd R[NC];
 #pragma unroll
   for (int u = 0; u < NC - 1; u++)
@@ -58,7 +58,7 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
   const int lc = mine ? dev::sink_cols(a, j)[a.off_f[f] + n - 1] : 0;
 #pragma unroll
   for (int i = 0; i < NC; i++) {
-    const int li = i < n - 1 ? arow[i < n - 1 ? i : 0] : a.mem_lab[((int64_t)m * a.F + f) * 2];
+    const int li = i < n - 1 ? arow[i < n - 1 ? i : 0] : a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK];
     c[i] = (mine && i < n) ? dev::ldS(S + (size_t)li * L + lc) : make_double2(0.0, 0.0);
   }
   unsigned piv = 0;  // rows already used as pivots
@@ -225,7 +225,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       const int rho = a.fam_rank[(int64_t)W * a.F + f];
       bool cf = false;
       const double2 d = dev::dispatch_member<NCMAX>(
-          n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * 2,
+          n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK,
           cols + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, ey[f], a.kc, &cf);
       if (cf) {
         fail |= 1u << f;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pai
                                               Y, T, &ey, a.kp);
       if (!fail) {
         d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f],
-                                        a.mem_lab + ((int64_t)m * a.F + f) * 2, col, Y, T, ey,
+                                        a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK, col, Y, T, ey,
                                         a.kc, &fail);
       }
       if (fail) {
@@ -368,7 +368,7 @@ __device__ __forceinline__ void kfac_one(const FwdArgs& a, int64_t t, int64_t n_
   const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
-  if (rho == 2 && sig == 2) {  // two changed rows and columns: one-sided update
+  if ((rho == 2 && sig == 2) || rho >= 3) {  // one-sided update for these blocks
     a.kguard[t] = 1;
     return;
   }
@@ -483,7 +483,7 @@ __device__ __forceinline__ void kfac_group_one(const FwdArgs& a, int64_t t) {
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
   bool gd;
-  if (rho == 2 && sig == 2)  // two changed rows and columns: one-sided update
+  if ((rho == 2 && sig == 2) || rho >= 3)  // one-sided update for these blocks
     gd = true;
   else if (sig == 2)
     gd = dev::group_kfac_block12<KG::G>(S, L, n, arow, scol, K, a.kp, g, gm, Bs, Ps);

@@ -29,7 +29,7 @@ struct FwdArgs {
   const int32_t* fam_arow;   // [W][Tn]
   const int32_t* mem_term;   // [members]
   const int32_t* mem_par;    // [members] bit f = sign parity of flavour f
-  const int32_t* mem_lab;    // [members][F][2]
+  const int32_t* mem_lab;    // [members][F][MHC_MAX_RANK]
   const int32_t* snk_lab;    // [n_snk][Tn]
   const double* w_src;
   const double* w_snk;
@@ -74,6 +74,9 @@ __device__ __forceinline__ bool dispatch_shared(int n, int rho, const cd* S, int
       break;
   }
 #undef MHC_SR
+  if constexpr (NCMAX >= 14) {  // three changed rows (n_f >= 14 only)
+    if (rho == 3) return shared_rows<NCMAX, 0, 3>(S, L, n, arow, col, Y, ys, ey, kp);
+  }
   return rho == 1 ? shared_rows<NCMAX, 0, 1>(S, L, n, arow, col, Y, ys, ey, kp)
                   : shared_rows<NCMAX, 0, 2>(S, L, n, arow, col, Y, ys, ey, kp);
 }
@@ -97,6 +100,9 @@ __device__ __forceinline__ cd dispatch_member(int n, int rho, const cd* S, int L
       break;
   }
 #undef MHC_MD
+  if constexpr (NCMAX >= 14) {  // three changed rows (n_f >= 14 only)
+    if (rho == 3) return member_det<NCMAX, 0, 3>(S, L, n, lab, col, Y, ys, ey, kc, fail);
+  }
   if constexpr (NCMAX >= 18) {  // the n of the large-nucleus and batched workloads
     if (n == 9)
       return rho == 1 ? member_det<9, 9, 1>(S, L, 9, lab, col, Y, ys, ey, kc, fail)
@@ -203,7 +209,7 @@ __device__ __forceinline__ void member_rows(const FwdArgs& a, int W, int m, int 
   const int n = a.n_f[f];
   const int32_t* ar = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
   for (int i = 0; i < n - rho; i++) rows[i] = ar[i];
-  for (int t = 0; t < rho; t++) rows[n - rho + t] = a.mem_lab[((int64_t)m * a.F + f) * 2 + t];
+  for (int t = 0; t < rho; t++) rows[n - rho + t] = a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + t];
 }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {

@@ -28,7 +28,7 @@ struct DevicePlan {
   int32_t* fam_arow = nullptr;   // [W][Tn]: shared-row labels first, then unused
   int32_t* mem_term = nullptr;   // [n_src] source term index of each member
   int32_t* mem_par = nullptr;    // [n_src] bit f: sign parity of flavour f
-  int32_t* mem_lab = nullptr;    // [n_src][F][2]
+  int32_t* mem_lab = nullptr;    // [n_src][F][MHC_MAX_RANK]
   int32_t* snk_lab = nullptr;    // [n_snk][Tn]
   int32_t* src_member = nullptr; // [n_src] member slot of each source term
   int32_t* mem_family = nullptr; // [n_src] family of each member slot
@@ -86,13 +86,13 @@ struct Plan {
   int64_t n_fam = 0;
   std::vector<int64_t> fam_off;          // [W+1]
   std::vector<int32_t> fam_rank;         // [W][F]
-  std::vector<int32_t> fam_rows;         // [W][F][2]
+  std::vector<int32_t> fam_rows;         // [W][F][MHC_MAX_RANK]
   std::vector<int32_t> fam_ref;          // [W][Tn]
   std::vector<int32_t> fam_arow;         // [W][Tn]
   std::vector<int64_t> mem_term;         // [n_src]
   std::vector<int32_t> mem_sign;         // [n_src] +-1 (product over flavours)
   std::vector<int32_t> mem_par;          // [n_src] bit f: sign parity of flavour f
-  std::vector<int32_t> mem_lab;          // [n_src][F][2]
+  std::vector<int32_t> mem_lab;          // [n_src][F][MHC_MAX_RANK]
   std::vector<int32_t> src_member;       // [n_src] member slot of each source term
   std::vector<int32_t> mem_family;       // [n_src]
   int max_members = 0;

@@ -25,6 +25,7 @@ constexpr size_t kBucketWindow = 2048;
 // a rank-2 update (4 dot products per member over n - 2 shared rows) saves too little over
 // splitting the family.
 constexpr int kRank2MinN = 10;
+constexpr int kRank3MinN = 14;  // three changed rows only for n_f >= 14 (opts.rank3)
 
 uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
@@ -121,6 +122,7 @@ double flops_shared_rows(int n, int rho) {
 double flops_member(int n, int rho) {
   if (n <= 0) return 0.0;
   const double dot = 6.0 + 8.0 * (n - 1);
+  if (rho == 3) return 9.0 * dot + 3.0 * 14.0 + 22.0 + 6.0;  // 3x3 det by cofactors, times sd
   return rho == 2 ? 4.0 * dot + 2.0 * 6.0 + 2.0 : dot;
 }
 
@@ -323,8 +325,13 @@ mhc_status build_plan(Plan& p) {
   const int rank2 = p.opts.rank2 ? 1 : 0;
   const int kmax = p.opts.max_family;
 
-  std::vector<int> dmax(F);
-  for (int f = 0; f < F; f++) dmax[f] = (rank2 && p.n_f[f] >= kRank2MinN) ? 2 : 1;
+  // changed labels allowed per flavour: sources up to 3 (opts.rank3), sinks up to 2
+  std::vector<int> dmax(F), dmax_snk(F);
+  for (int f = 0; f < F; f++) {
+    dmax[f] = (rank2 && p.n_f[f] >= kRank2MinN) ? 2 : 1;
+    if (rank2 && p.opts.rank3 && p.n_f[f] >= kRank3MinN) dmax[f] = 3;
+    dmax_snk[f] = std::min(dmax[f], 2);
+  }
   int64_t edges = 0;
   std::vector<std::vector<int32_t>> dom_sets =
       dominated_sets(p.labels_src, N, F, p.n_f, p.off_f, Tn, dmax, &edges);
@@ -341,7 +348,7 @@ mhc_status build_plan(Plan& p) {
   p.mem_lab.clear();
   p.src_member.assign(N, -1);
   p.mem_family.clear();
-  int64_t rank2_blocks = 0;
+  int64_t rank2_blocks = 0, rank3_blocks = 0;
   p.max_members = 0;
 
   struct Member {
@@ -393,7 +400,7 @@ mhc_status build_plan(Plan& p) {
     }
     for (auto& g : groups) {
       const int64_t W = p.n_fam++;
-      std::vector<int32_t> ranks(F), rows(2 * F, -1), arow(Tn, -1);
+      std::vector<int32_t> ranks(F), rows(MHC_MAX_RANK * F, -1), arow(Tn, -1);
       std::vector<int> eps(F, 0);
       for (int f = 0; f < F; f++) {
         const int n = p.n_f[f];
@@ -405,7 +412,8 @@ mhc_status build_plan(Plan& p) {
         if (R.empty()) R.push_back(n - 1);
         ranks[f] = (int32_t)R.size();
         if (R.size() == 2) rank2_blocks++;
-        for (size_t k = 0; k < R.size(); k++) rows[2 * f + k] = R[k];
+        if (R.size() == 3) rank3_blocks++;
+        for (size_t k = 0; k < R.size(); k++) rows[MHC_MAX_RANK * f + k] = R[k];
         // [shared rows ascending; changed rows ascending] and the sign of that reordering
         std::vector<int> order;
         int a = 0;
@@ -425,13 +433,13 @@ mhc_status build_plan(Plan& p) {
       for (int mi : g.members) {
         const Member& m = mems[mi];
         int parity = 0, bits = 0;
-        std::vector<int32_t> lab(2 * F, -1);
+        std::vector<int32_t> lab(MHC_MAX_RANK * F, -1);
         for (int f = 0; f < F; f++) {
           if (p.n_f[f] == 0) continue;
           const int pf = m.al[f].parity ^ eps[f];
           parity ^= pf;
           bits |= pf << f;
-          for (int k = 0; k < ranks[f]; k++) lab[2 * f + k] = m.al[f].aligned[g.R[f][k]];
+          for (int k = 0; k < ranks[f]; k++) lab[MHC_MAX_RANK * f + k] = m.al[f].aligned[g.R[f][k]];
         }
         p.mem_lab.insert(p.mem_lab.end(), lab.begin(), lab.end());
         p.src_member[m.term] = (int32_t)p.mem_term.size();
@@ -452,7 +460,7 @@ mhc_status build_plan(Plan& p) {
     int64_t sedges = 0;
     std::vector<std::vector<int32_t>> sink_sets =
         p.opts.one_sided ? std::vector<std::vector<int32_t>>()
-                         : dominated_sets(p.labels_snk, p.n_snk, F, p.n_f, p.off_f, Tn, dmax, &sedges);
+                         : dominated_sets(p.labels_snk, p.n_snk, F, p.n_f, p.off_f, Tn, dmax_snk, &sedges);
     if (p.opts.one_sided)
       for (int64_t j = 0; j < p.n_snk; j++) sink_sets.push_back({(int32_t)j});
     struct SGroup {
@@ -478,7 +486,7 @@ mhc_status build_plan(Plan& p) {
             std::set<int> u(g.R[f].begin(), g.R[f].end());
             u.insert(ch[f].begin(), ch[f].end());
             U[f].assign(u.begin(), u.end());
-            ok = (int)U[f].size() <= dmax[f];
+            ok = (int)U[f].size() <= dmax_snk[f];
           }
           if (!ok) continue;
           g.R = U;
@@ -544,6 +552,7 @@ mhc_status build_plan(Plan& p) {
   s.dominators = (int64_t)dom_sets.size();
   s.families = p.n_fam;
   s.rank2_family_flavours = rank2_blocks;
+  s.rank3_family_flavours = rank3_blocks;
   s.members = (int64_t)p.mem_term.size();
   s.graph_edges = edges;
   s.sink_families = p.n_qfam;
@@ -579,10 +588,12 @@ mhc_status build_plan(Plan& p) {
         fl += (double)qc1[f] * flops_adjugate(n - 1) + (double)qs1[f] * flops_kapply(n);
         fl += (double)qc2[f] * flops_block12(n) + (double)qs2[f] * flops_kapply12(n);
         two_blocks += qc1[f] + qc2[f];
-      } else {
+      } else if (rho == 2) {
         fl += (double)qc1[f] * flops_rank2_block(n) + (double)qs1[f] * flops_kapply2(n);
         fl += (double)qs2[f] * flops_shared_rows(n, rho);  // two changed rows and columns
         two_blocks += qc1[f];
+      } else {  // three changed rows: every sink one-sided
+        fl += (double)(qs1[f] + qs2[f]) * flops_shared_rows(n, rho);
       }
     }
   }

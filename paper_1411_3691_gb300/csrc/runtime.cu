@@ -75,7 +75,7 @@ int plan_tile(const Plan& p) {
   return p.max_n <= 8 ? 128 : (p.max_n <= 12 ? 64 : 32);
 }
 
-// y-cache slots per flavour: n for rank-1 families, 2n + 1 when some family is rank 2
+// y-cache slots per flavour: n for rank-1 families, r n + 1 when some family has rank r >= 2
 void plan_slots(const Plan& p, int* yoff, int* total) {
   int s = 0;
   for (int f = 0; f < p.F; f++) {
@@ -83,7 +83,7 @@ void plan_slots(const Plan& p, int* yoff, int* total) {
     for (int64_t W = 0; W < p.n_fam; W++) r = std::max(r, (int)p.fam_rank[W * p.F + f]);
     yoff[f] = s;
     const int n = p.n_f[f];
-    s += (r == 2) ? 2 * n + 1 : n;
+    s += (r >= 2) ? r * n + 1 : n;  // rank r >= 2: r null vectors and sd
   }
   *total = std::max(s, 1);
 }

@@ -20,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libmhc.so")
 
 MHC_OK, MHC_EINVAL, MHC_ENOMEM, MHC_ECUDA, MHC_ETIMEOUT, MHC_ENONFINITE, MHC_EUNSUPPORTED = range(7)
+MHC_MAX_RANK = 3  # stride of the changed-row tables (include/mhc.h)
 STATUS_NAMES = ["MHC_OK", "MHC_EINVAL", "MHC_ENOMEM", "MHC_ECUDA", "MHC_ETIMEOUT",
                 "MHC_ENONFINITE", "MHC_EUNSUPPORTED"]
 MHC_NMAX = 32
@@ -43,7 +44,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("tau_parent", ctypes.c_double), ("tau_child", ctypes.c_double),
                 ("sink_tile", ctypes.c_int32), ("rank2", ctypes.c_int32),
                 ("max_family", ctypes.c_int32), ("one_sided", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("rank3", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +56,7 @@ class Stats(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("refactor_parent", ctypes.c_int64),
                 ("refactor_child", ctypes.c_int64), ("sink_families", ctypes.c_int64),
                 ("two_sided_blocks", ctypes.c_int64), ("backward_flops_per_call", ctypes.c_double),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("rank3_family_flavours", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -181,11 +182,11 @@ def mhc_plan_families(plan, F: int, Tn: int, n_src: int) -> dict:
     W = nW.value
     off = np.zeros(W + 1, np.int64)
     rank = np.zeros((W, F), np.int32)
-    rows = np.zeros((W, F, 2), np.int32)
+    rows = np.zeros((W, F, MHC_MAX_RANK), np.int32)
     ref = np.zeros((W, Tn), np.int32)
     term = np.zeros(n_src, np.int64)
     sign = np.zeros(n_src, np.int32)
-    labs = np.zeros((n_src, F, 2), np.int32)
+    labs = np.zeros((n_src, F, MHC_MAX_RANK), np.int32)
     _check(L.mhc_plan_families(_vp(plan), ctypes.byref(nW), off.ctypes.data_as(_i64p), rank.ctypes.data_as(_i32p),
                                rows.ctypes.data_as(_i32p), ref.ctypes.data_as(_i32p), term.ctypes.data_as(_i64p),
                                sign.ctypes.data_as(_i32p), labs.ctypes.data_as(_i32p)))

@@ -224,3 +224,22 @@ def test_complex_weights(M):
     ref = parts["ac"] - parts["bd"] + 1j * (parts["ad"] + parts["bc"])
     assert abs(got - ref) <= 1e-11 * scale, (got, ref)
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+
+
+@pytest.mark.parametrize("one_sided", [0, 1])
+def test_three_row_families(M, one_sided):
+    """Rank-3 families (opts.rank3, n_f >= 14): C against the oracle, with sink families
+    (the rank-3 blocks take the one-sided path) and without, and every pair's determinants
+    through the probe."""
+    w = wl.make_workload("r3", [14, 14], [56, 56], [6, 5, 4, 7], [5, 6, 4, 20], seed=67, two_row_frac=0.2,
+                         three_row_frac=0.5)
+    opts = M.default_opts()
+    opts.rank3 = 1
+    opts.one_sided = one_sided
+    C, plan, S = gpu_C(M, w, opts)
+    assert plan.stats()["rank3_family_flavours"] > 0
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    ii, jj = np.meshgrid(np.arange(len(w.w_src)), np.arange(len(w.w_snk)), indexing="ij")
+    check_pairs(M, w, plan, S, ii.ravel(), jj.ravel())

@@ -61,7 +61,7 @@ def _walk(M, w, plan):
     return dets
 
 
-@pytest.mark.parametrize("name", ["deuteron", "helium4", "large", "mixed"])
+@pytest.mark.parametrize("name", ["deuteron", "helium4", "large", "mixed", "three_rows"])
 def test_plan_walk_matches_oracle(M, name):
     if name == "deuteron":
         w = wl.deuteron(scale=6 / 64)
@@ -72,9 +72,16 @@ def test_plan_walk_matches_oracle(M, name):
     elif name == "large":
         w = wl.make_workload("large-small", [10, 8], [40, 36], [12, 9, 7], [5, 4], diag=3.0, seed=5,
                              two_row_frac=0.5, forced_frac=0.2, twins=8)
-    else:
+    elif name == "mixed":
         w = wl.make_workload("mixed", [3, 0, 7], [24, 5, 30], [5, 1, 3, 8], [3, 3], seed=9, two_row_frac=0.3)
-    plan = M.Plan.from_workload(w)
+    else:
+        w = wl.make_workload("r3", [14, 10], [56, 40], [6, 5, 4], [4, 3], seed=61, two_row_frac=0.3,
+                             three_row_frac=0.6)
+    opts = M.default_opts()
+    opts.rank3 = 1 if name == "three_rows" else 0
+    plan = M.Plan.from_workload(w, opts)
+    if name == "three_rows":
+        assert plan.stats()["rank3_family_flavours"] > 0
     fam = plan.families()
     # every source term is a member exactly once
     assert sorted(fam["term"].tolist()) == list(range(plan.n_src))
