@@ -82,8 +82,7 @@ typedef struct {
   int32_t rank3;       /* 1 (with rank2): source families may also differ in three
                           rows per flavour with n_f >= 14 (rank-3 update: a 3x3
                           generalised cofactor with three null vectors; the
-                          general rank-k update of Sec. 5 taken to k = 3); the
-                          adjoint does not differentiate such plans.            0     */
+                          general rank-k update of Sec. 5 taken to k = 3).      0     */
   int32_t reserved[6];
 } mhc_plan_opts;
 
@@ -226,10 +225,10 @@ mhc_status mhc_correlator_cw(mhc_plan_t plan, const double* const* S_f, const do
  * which is PyTorch's convention for the gradient of a real loss.  g_out_dev is a device
  * pointer to 2 doubles.  Any of dS_f (the whole array or single entries), dw_src_dev or
  * dw_snk_dev may be NULL to skip that output.  The dS_f buffers must not alias each
- * other.  Two-row (rank-2) families are differentiated through the null vectors of their
- * shared rows; when those rows fail the pivot guard for some sink, that block's dS_f
- * contribution is left out and mhc_get_status returns MHC_EUNSUPPORTED (plan with
- * opts->rank2 = 0 for such inputs).  Not in the paper.
+ * other.  Families of two or three changed rows are differentiated through the null
+ * vectors of their shared rows; when those rows fail the pivot guard for some sink, that
+ * block's dS_f contribution is left out and mhc_get_status returns MHC_EUNSUPPORTED (plan
+ * with opts->rank2 = 0 for such inputs).  Not in the paper.
  */
 mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
                                    const double* w_src_dev, const double* w_snk_dev,

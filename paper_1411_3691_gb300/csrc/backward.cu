@@ -131,16 +131,10 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
     return MHC_EINVAL;
   }
   Plan& p = *reinterpret_cast<Plan*>(plan);
-  bool any_r2 = false;  // two-row families: two member rows per member, coefficient scratch
+  int max_rank = 1;  // families of rank k >= 2: k member rows per member, k^2 coefficients
   for (int64_t W = 0; W < p.n_fam; W++)
-    for (int f = 0; f < p.F; f++) {
-      any_r2 |= p.fam_rank[W * p.F + f] == 2;
-      if (p.fam_rank[W * p.F + f] >= 3) {
-        set_error("mhc_correlator_backward: the adjoint of three-row families is not built; "
-                  "plan with opts.rank3 = 0");
-        return MHC_EUNSUPPORTED;
-      }
-    }
+    for (int f = 0; f < p.F; f++) max_rank = std::max(max_rank, (int)p.fam_rank[W * p.F + f]);
+  const bool any_r2 = max_rank >= 2;
   mhc_status st = ensure_device(p);
   if (st != MHC_OK) return st;
   BwdArgs b;
@@ -168,7 +162,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   const size_t smem = smem_of(T);
   const int warps = T / 32;
   const int n_tiles = (int)((p.n_snk + T - 1) / T);
-  const int slots_max = Mmax + (any_r2 ? 2 : 1) * kmax;
+  const int slots_max = Mmax + max_rank * kmax;
   const size_t per_cta = (size_t)warps * F * slots_max * Lmax * sizeof(double2);
   int n_chunks = (int)std::min<int64_t>(n_tiles, std::max<int64_t>(1, (48 * 152 + p.n_fam - 1) / p.n_fam));
   while (n_chunks > 1 && (double)per_cta * p.n_fam * n_chunks > 1.0e9) n_chunks = (n_chunks + 1) / 2;
@@ -192,8 +186,8 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_accs), (size_t)ctas * kmax * T,
                       &d.bwd_accs_bytes)) != MHC_OK)
     return st;
-  if (any_r2 && (st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_r2), (size_t)ctas * kmax * 4 * T,
-                                &d.bwd_r2_bytes)) != MHC_OK)
+  if (any_r2 && (st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_r2),
+                                (size_t)ctas * kmax * max_rank * max_rank * T, &d.bwd_r2_bytes)) != MHC_OK)
     return st;
   // row-label index of the accumulators, per flavour: label -> (family, slot) pairs
   if (d.bwd_index.empty()) {
@@ -245,6 +239,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.stage = reinterpret_cast<double2*>(d.bwd_stage);
   b.accs = reinterpret_cast<double2*>(d.bwd_accs);
   b.r2 = reinterpret_cast<double2*>(d.bwd_r2);
+  b.rk2 = max_rank * max_rank;
   const int nc = plan_ncmax(p);
   b.kinv = nullptr;
   if (b.a.snk_orig) {  // two-sided blocks: the factors of B, then B^{-1} for the cofactors

@@ -32,7 +32,8 @@ struct BwdArgs {
   double2* dwsnk_part;  // [W][n_snk]
   double2* stage;       // [cta][T][mn_max] shared-row cofactors of each sink, per block
   double2* accs;        // [cta][kmax][T] dw_src accumulators of each sink, per block
-  double2* r2;          // [cta][kmax][4][T] member-row coefficients of two-row families
+  double2* r2;          // [cta][kmax][rk2][T] member-row coefficients of rank-2/3 families
+  int rk2;              // coefficients per member: (largest rank)^2
   const double2* kinv;  // [W][Q][kistride]: B^{-1} row-major per flavour (two-sided blocks)
   int kistride;
   int kioff[MHC_FMAX];
@@ -344,60 +345,100 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
   }
 }
 
-// Two-row family (rank 2), shared rows A ((n-2) x n), member rows b1, b2: G = [A; b1; b2].
-// With the null vectors z1, z2 of A (last two coordinates the identity), sd = sign(P)
-// det(A1) and D = [b1; b2] [z1 z2], det G = sd det(D), and Jacobi's formula gives
-//   cof(G)[b1] = sd (z1 D11 - z2 D10),   cof(G)[b2] = sd (z2 D00 - z1 D01),
+// Family of rank k (k = 2, 3 changed rows), shared rows A ((n-k) x n), member rows
+// b_0..b_{k-1}: G = [A; B].  With the null vectors z_v of A (last k coordinates the
+// identity), sd = sign(P) det(A1) and D = B Z (k x k), det G = sd det(D), and from
+// cof(G) = det(G) G^{-T} (G^{-1}'s A-columns X = X0 - Z D^{-1} B X0 with the right inverse
+// X0 = [A1^{-1}; 0], det(D) D^{-1} = adj D):
+//   cof(G)[b_a] = sd Z adj(D) e_a,
 //   sum_c gamma_c cof(G_c)[A] = sd X0^T (s I - E Z^T),
-// X0 = [A1^{-1}; 0; 0] (a right inverse of A), s = sum_c gamma_c det(D_c),
-// E = sum_c gamma_c [b1 b2] adj(D_c)^T (n x 2): row m of the shared block is
-//   sd [ s (u_m; 0; 0) - (u_m . E0) z1 - (u_m . E1) z2 ],  u_m = A1^{-1} e_m,
-// O(n) per member and no division by det G.  Writes the shared block to Mst (row-major
-// (n-2) x n) and the member rows' coefficients on (z1, z2) -- gamma sd (D11, -D10) for
-// b1, gamma sd (-D01, D00) for b2 -- to R2[c][4][T].  When the shared rows fail the pivot
-// guard the block is not differentiated: the outputs are zero and the status reports it.
-template <int NC>
-__device__ __noinline__ void cof_pass2(const FwdArgs& a, int f, int n, int mem0, int kW, double wj,
-                                       int tid, int T, int kmax, const int32_t* __restrict__ col,
+// s = sum_c gamma_c det(D_c), E = sum_c gamma_c B_c^T adj(D_c)^T (n x k): row m of the
+// shared block is sd [ s (u_m; 0) - sum_v (u_m . E_v) z_v ],  u_m = A1^{-1} e_m, O(n) per
+// member and no division by det G.  Writes the shared block to Mst (row-major
+// (n-k) x n) and member row a's coefficients on z_v, gamma sd adj(D)[v][a], to
+// R[c][a k + v][T].  When the shared rows fail the pivot guard the block is not
+// differentiated: the outputs are zero and the status reports it.
+template <int RK>
+__device__ __forceinline__ void adjugate(const cd (&D)[RK][RK], cd (&adj)[RK][RK], cd* det) {
+  if constexpr (RK == 2) {
+    adj[0][0] = D[1][1];
+    adj[0][1] = dev::cneg(D[0][1]);
+    adj[1][0] = dev::cneg(D[1][0]);
+    adj[1][1] = D[0][0];
+    *det = dev::cfms(D[0][1], D[1][0], dev::cmul(D[0][0], D[1][1]));
+  } else {
+    // adj[j][i] = (-1)^(i+j) minor(i, j)
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const int r0 = i == 0 ? 1 : 0, r1 = i == 2 ? 1 : 2;
+        const int c0 = j == 0 ? 1 : 0, c1 = j == 2 ? 1 : 2;
+        const cd m = dev::cfms(D[r0][c1], D[r1][c0], dev::cmul(D[r0][c0], D[r1][c1]));
+        adj[j][i] = ((i + j) & 1) ? dev::cneg(m) : m;
+      }
+    *det = dev::cfma(D[0][2], adj[2][0], dev::cfma(D[0][1], adj[1][0], dev::cmul(D[0][0], adj[0][0])));
+  }
+}
+
+template <int NC, int RK>
+__device__ __noinline__ void cof_passk(const FwdArgs& a, int f, int n, int mem0, int kW, int tid,
+                                       int T, int kmax, const int32_t* __restrict__ col,
                                        const int32_t* __restrict__ arow, const cd* Dets, const cd* Y,
-                                       bool guarded, cd* Mst, cd* R2) {
-  const int M = n - 2;
+                                       bool guarded, cd* Mst, cd* R) {
+  const int M = n - RK;
   const cd* S = a.S[f];
   const int L = a.L_f[f];
-  const cd sd = Y[(size_t)2 * n * T];
-  cd E0[NC], E1[NC];
-  for (int q = 0; q < n; q++) E0[q] = E1[q] = make_double2(0.0, 0.0);
+  const cd sd = Y[(size_t)RK * n * T];
+  cd E[RK][NC];
+  for (int q = 0; q < n; q++)
+#pragma unroll
+    for (int v = 0; v < RK; v++) E[v][q] = make_double2(0.0, 0.0);
   cd s = make_double2(0.0, 0.0);
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
     const cd g = Dets[dix(c, f, kmax, T, tid)];  // gamma_c of this flavour
-    const cd* r1 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK] * L;
-    const cd* r2 = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + 1] * L;
-    cd d00 = make_double2(0.0, 0.0), d01 = d00, d10 = d00, d11 = d00;
+    const cd* r[RK];
+#pragma unroll
+    for (int u = 0; u < RK; u++) r[u] = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + u] * L;
+    cd D[RK][RK];
+#pragma unroll
+    for (int u = 0; u < RK; u++)
+#pragma unroll
+      for (int v = 0; v < RK; v++) D[u][v] = make_double2(0.0, 0.0);
     for (int q = 0; q < n; q++) {
-      const cd b1 = dev::ldS(r1 + col[q]), b2 = dev::ldS(r2 + col[q]);
-      const cd z1 = Y[(size_t)q * T], z2 = Y[(size_t)(n + q) * T];
-      d00 = dev::cfma(b1, z1, d00);
-      d01 = dev::cfma(b1, z2, d01);
-      d10 = dev::cfma(b2, z1, d10);
-      d11 = dev::cfma(b2, z2, d11);
+#pragma unroll
+      for (int u = 0; u < RK; u++) {
+        const cd b = dev::ldS(r[u] + col[q]);
+#pragma unroll
+        for (int v = 0; v < RK; v++) D[u][v] = dev::cfma(b, Y[(size_t)(v * n + q) * T], D[u][v]);
+      }
     }
-    s = dev::cfma(g, dev::cfms(d01, d10, dev::cmul(d00, d11)), s);
-    const cd g00 = dev::cmul(g, d00), g01 = dev::cmul(g, d01), g10 = dev::cmul(g, d10), g11 = dev::cmul(g, d11);
-    for (int q = 0; q < n; q++) {
-      const cd b1 = dev::ldS(r1 + col[q]), b2 = dev::ldS(r2 + col[q]);
-      E0[q] = dev::cfms(b2, g01, dev::cfma(b1, g11, E0[q]));
-      E1[q] = dev::cfms(b1, g10, dev::cfma(b2, g00, E1[q]));
+    cd adj[RK][RK], det;
+    adjugate<RK>(D, adj, &det);
+    s = dev::cfma(g, det, s);
+    cd ga[RK][RK];  // gamma adj(D)
+#pragma unroll
+    for (int u = 0; u < RK; u++)
+#pragma unroll
+      for (int v = 0; v < RK; v++) ga[u][v] = dev::cmul(g, adj[u][v]);
+    for (int q = 0; q < n; q++) {  // E_v += gamma sum_a b_a adj(D)[v][a]
+#pragma unroll
+      for (int u = 0; u < RK; u++) {
+        const cd b = dev::ldS(r[u] + col[q]);
+#pragma unroll
+        for (int v = 0; v < RK; v++) E[v][q] = dev::cfma(b, ga[v][u], E[v][q]);
+      }
     }
-    const cd gs = dev::cmul(g, sd);
-    cd* R = R2 + (size_t)c * 4 * T + tid;
-    R[0] = guarded ? make_double2(0.0, 0.0) : dev::cmul(gs, d11);
-    R[(size_t)T] = guarded ? make_double2(0.0, 0.0) : dev::cneg(dev::cmul(gs, d10));
-    R[(size_t)2 * T] = guarded ? make_double2(0.0, 0.0) : dev::cneg(dev::cmul(gs, d01));
-    R[(size_t)3 * T] = guarded ? make_double2(0.0, 0.0) : dev::cmul(gs, d00);
+    cd* Rc = R + (size_t)c * RK * RK * T + tid;
+#pragma unroll
+    for (int u = 0; u < RK; u++)
+#pragma unroll
+      for (int v = 0; v < RK; v++)
+        Rc[(size_t)(u * RK + v) * T] = guarded ? make_double2(0.0, 0.0) : dev::cmul(sd, ga[v][u]);
   }
-  // LU of A1 (the shared rows on the first n - 2 columns), partial pivoting
-  constexpr int MC = NC - 2 > 0 ? NC - 2 : 1;
+  // LU of A1 (the shared rows on the first n - k columns), partial pivoting
+  constexpr int MC = NC - RK > 0 ? NC - RK : 1;
   cd A[MC][MC];
   int perm[MC];
   for (int i = 0; i < M; i++) {
@@ -443,9 +484,10 @@ __device__ __noinline__ void cof_pass2(const FwdArgs& a, int f, int n, int mem0,
     atomicOr(&a.counters[0], kStatusUnsupported);
     for (int e = 0; e < M * n; e++) Mst[e] = make_double2(0.0, 0.0);
     for (int c = 0; c < kW; c++)
-      for (int t = 0; t < 4; t++) R2[((size_t)c * 4 + t) * T + tid] = make_double2(0.0, 0.0);
+      for (int t = 0; t < RK * RK; t++) R[((size_t)c * RK * RK + t) * T + tid] = make_double2(0.0, 0.0);
     return;
   }
+  const cd ss = dev::cmul(sd, s);
   for (int i = 0; i < M; i++) {  // u = column perm[i] of A1^{-1} = U^{-1} L^{-1} e_i
     cd u[MC];
     for (int p = 0; p < M; p++) {
@@ -464,42 +506,45 @@ __device__ __noinline__ void cof_pass2(const FwdArgs& a, int f, int n, int mem0,
       for (int t = p + 1; t < M; t++) w = dev::cfms(A[p][t], u[t], w);
       u[p] = dev::cmul(w, rc[p]);
     }
-    cd e0 = make_double2(0.0, 0.0), e1 = e0;
-    for (int q = 0; q < M; q++) {
-      e0 = dev::cfma(u[q], E0[q], e0);
-      e1 = dev::cfma(u[q], E1[q], e1);
+    cd se[RK];
+#pragma unroll
+    for (int v = 0; v < RK; v++) {
+      cd e = make_double2(0.0, 0.0);
+      for (int q = 0; q < M; q++) e = dev::cfma(u[q], E[v][q], e);
+      se[v] = dev::cmul(sd, e);
     }
-    const cd se0 = dev::cmul(sd, e0), se1 = dev::cmul(sd, e1), ss = dev::cmul(sd, s);
     cd* row = Mst + (size_t)perm[i] * n;
     for (int q = 0; q < M; q++) {
-      const cd z1 = Y[(size_t)q * T], z2 = Y[(size_t)(n + q) * T];
-      row[q] = dev::cfms(se1, z2, dev::cfms(se0, z1, dev::cmul(ss, u[q])));
+      cd x = dev::cmul(ss, u[q]);
+#pragma unroll
+      for (int v = 0; v < RK; v++) x = dev::cfms(se[v], Y[(size_t)(v * n + q) * T], x);
+      row[q] = x;
     }
-    row[M] = dev::cneg(se0);
-    row[M + 1] = dev::cneg(se1);
+#pragma unroll
+    for (int v = 0; v < RK; v++) row[M + v] = dev::cneg(se[v]);  // z_v's unit coordinates
   }
 }
 
-// Scatter of one warp's sinks for a two-row family (flavour f): lane s owns row s -- a
-// shared row (s < n - 2, from the staged block) or member (s - n + 2) / 2's first or
-// second changed row, whose values are coefficient combinations of the cached z1, z2.
-// Same fixed order and shared-column sums as scatter_rows.
-template <int NC>
-__device__ __noinline__ void scatter_rows2(const FwdArgs& a, const BwdArgs& B, int f, int n, int kW,
+// Scatter of one warp's sinks for a family of rank k (flavour f): lane s owns row s -- a
+// shared row (s < n - k, from the staged block) or row a of member c (s = n - k + k c + a),
+// whose values are the coefficient combination sum_v R[c][a k + v] z_v.  Same fixed order
+// and shared-column sums as scatter_rows.
+template <int NC, int RK>
+__device__ __noinline__ void scatter_rowsk(const FwdArgs& a, const BwdArgs& B, int f, int n, int kW,
                                            int nlive, int T, int warp, int lane,
                                            const int32_t* __restrict__ mycol, int myQ, int mynsh,
-                                           const cd* Stage, const cd* Ysm, const cd* R2, cd* Df) {
+                                           const cd* Stage, const cd* Ysm, const cd* R, cd* Df) {
   constexpr unsigned FULL = 0xffffffffu;
-  const int M = n - 2;
-  const int nslots = M + 2 * kW;
+  const int M = n - RK;
+  const int nslots = M + RK * kW;
   int cl[NC];
 #pragma unroll
   for (int q = 0; q < NC; q++) cl[q] = q < n ? mycol[q] : 0;
   for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
     const bool act = s < nslots;
     const bool mem = s >= M;
-    const int c = act && mem ? (s - M) >> 1 : 0;
-    const int t = act && mem ? (s - M) & 1 : 0;
+    const int c = act && mem ? (s - M) / RK : 0;
+    const int t = act && mem ? (s - M) - RK * c : 0;
     cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
     cd acc[NC];
     int curlab[NC];
@@ -537,18 +582,21 @@ __device__ __noinline__ void scatter_rows2(const FwdArgs& a, const BwdArgs& B, i
         }
       }
       const int ts = warp * 32 + jl;
-      cd k0 = make_double2(0.0, 0.0), k1 = k0;
-      if (mem) {
-        k0 = R2[((size_t)c * 4 + 2 * t) * T + ts];
-        k1 = R2[((size_t)c * 4 + 2 * t + 1) * T + ts];
-      }
+      cd k[RK];
+#pragma unroll
+      for (int v = 0; v < RK; v++)
+        k[v] = mem ? R[((size_t)c * RK * RK + t * RK + v) * T + ts] : make_double2(0.0, 0.0);
       const cd* st = Stage + (size_t)ts * B.mn_max + (mem ? 0 : s * n);
 #pragma unroll
       for (int q = 0; q < NC; q++) {
         if (q >= n) break;
-        const cd v = mem ? dev::cfma(k1, Ysm[(size_t)(a.yoff[f] + n + q) * T + ts],
-                                     dev::cmul(k0, Ysm[(size_t)(a.yoff[f] + q) * T + ts]))
-                         : st[q];
+        cd v = make_double2(0.0, 0.0);
+        if (mem) {
+#pragma unroll
+          for (int u = 0; u < RK; u++) v = dev::cfma(k[u], Ysm[(size_t)(a.yoff[f] + u * n + q) * T + ts], v);
+        } else {
+          v = st[q];
+        }
         if (q < nsh) {
           acc[q] = dev::cadd(acc[q], v);
         } else if (act) {
@@ -805,16 +853,28 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int32_t* col = cols + a.off_f[f];
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
       if constexpr (NCMAX >= 10) {
-        if (a.fam_rank[(int64_t)W * a.F + f] == 2) {  // two-row family
-          cd* R2 = B.r2 + (size_t)cta * B.kmax * 4 * T;
-          cof_pass2<NCMAX>(a, f, n, mem0, kW, wj, tid, T, B.kmax, col, arow, Dets,
-                           Ysm + (size_t)a.yoff[f] * T + tid, (pguard >> f) & 1, myStage, R2);
+        const int rho = a.fam_rank[(int64_t)W * a.F + f];
+        if (rho >= 2) {  // two or three changed rows
+          cd* Rk = B.r2 + (size_t)cta * B.kmax * B.rk2 * T;
+          const cd* Yf = Ysm + (size_t)a.yoff[f] * T + tid;
+          const bool gd = (pguard >> f) & 1;
+          if (rho == 2) {
+            cof_passk<NCMAX, 2>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk);
+          } else if constexpr (NCMAX >= 14) {
+            cof_passk<NCMAX, 3>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk);
+          }
           __syncwarp();
           const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
           const int nlive = rem < 32 ? (int)rem : 32;
           const int mynsh = qtwo ? n - a.q_rank[(int64_t)Q * a.F + f] : 0;
-          scatter_rows2<NCMAX>(a, B, f, n, kW, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh, Stage, Ysm,
-                               R2, Dw + (size_t)f * B.slots_max * B.Lmax);
+          cd* Df = Dw + (size_t)f * B.slots_max * B.Lmax;
+          if (rho == 2) {
+            scatter_rowsk<NCMAX, 2>(a, B, f, n, kW, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh, Stage, Ysm,
+                                    Rk, Df);
+          } else if constexpr (NCMAX >= 14) {
+            scatter_rowsk<NCMAX, 3>(a, B, f, n, kW, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh, Stage, Ysm,
+                                    Rk, Df);
+          }
           __syncwarp();
           continue;
         }

@@ -617,18 +617,20 @@ mhc_status build_plan(Plan& p) {
       one += inv + M * (8.0 * M + 6.0) + M * M * 14.0;                          // eta, beta, cofactor rows
       const double two = 8.0 * n - 2.0 + M * (22.0 * M + 6.0);                  // h.y, eta, cofactor rows
       const double scat = M * n * 2.0 + k * n * 8.0;  // the members' gamma comes with h (gh)
-      if (p.fam_rank[W * F + f] == 2) {
-        // two-row family: per member D = [b1; b2][z1 z2], det D, s, E, the member rows'
-        // coefficients; per sink the LU of A1 ((n-2) x (n-2)), the columns of A1^{-1}, the
-        // shared block rows; the scatter of 2k member rows and n-2 shared rows
-        const double M2 = n - 2;
-        double r2 = k * (64.0 * n + 6.0 * std::max(F - 1, 0) + 71.0);
-        r2 += flops_adjugate((int)M2);
-        for (int i = 0; i < (int)M2; i++)
-          r2 += 8.0 * (M2 - i - 1) * (M2 - i - 2) / 2.0 + 8.0 * M2 * (M2 - 1) / 2.0 + 6.0 * M2;
-        r2 += M2 * (38.0 * M2 + 18.0);
-        r2 += 2.0 * k * n * 16.0 + 2.0 * M2 * n;
-        bfl += (double)p.n_snk * r2;
+      const int rk = p.fam_rank[W * F + f];
+      if (rk >= 2) {
+        // rank k = 2, 3: per member D = B Z (k^2 dots), adj(D) and det D, s, E, the member
+        // rows' coefficients; per sink the LU of A1 ((n-k) x (n-k)), the columns of A1^{-1},
+        // the shared block rows; the scatter of k per member rows and n-k shared rows
+        const double K = rk, Mk = n - rk;
+        const double adj = rk == 2 ? 6.0 + 8.0 : 9.0 * 14.0 + 22.0;
+        double rr = k * (2.0 * K * K * 8.0 * n + adj + 8.0 + 2.0 * K * K * 6.0);
+        rr += flops_adjugate((int)Mk);
+        for (int i = 0; i < (int)Mk; i++)
+          rr += 8.0 * (Mk - i - 1) * (Mk - i - 2) / 2.0 + 8.0 * Mk * (Mk - 1) / 2.0 + 6.0 * Mk;
+        rr += Mk * (K * (8.0 * Mk + 6.0) + 6.0 + Mk * (6.0 + 8.0 * K));
+        rr += K * k * n * 8.0 * K + 2.0 * Mk * n;
+        bfl += (double)p.n_snk * rr;
         continue;
       }
       bfl += (double)p.n_snk * (gh + scat);

@@ -255,17 +255,16 @@ def test_backward_families_of_64(M):
     check_vs_oracle(M, w, opts)
 
 
-def test_three_row_plans_are_refused(M):
-    """The adjoint of rank-3 families is not built: the call says so before launching."""
+def test_three_row_families(M):
+    """Rank-3 families (opts.rank3, n_f >= 14): the adjoint against the oracle's Jacobi
+    gradient, with and without sink families."""
     w = wl.make_workload("r3", [14, 10], [56, 40], [6, 5, 4], [4, 3], seed=61, two_row_frac=0.3,
                          three_row_frac=0.6)
-    opts = M.default_opts()
-    opts.rank3 = 1
-    plan = M.Plan.from_workload(w, opts)
-    assert plan.stats()["rank3_family_flavours"] > 0
-    S = dev_S(w)
-    g = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
-    with pytest.raises(M.MHCError) as e:
-        M.mhc_correlator_backward(plan.handle, S, g, None, None, [torch.empty_like(s) for s in S], None, None)
-    assert e.value.status == M.MHC_EUNSUPPORTED
-    plan.close()
+    for one_sided in (0, 1):
+        opts = M.default_opts()
+        opts.rank3 = 1
+        opts.one_sided = one_sided
+        plan = M.Plan.from_workload(w, opts)
+        assert plan.stats()["rank3_family_flavours"] > 0
+        plan.close()
+        check_vs_oracle(M, w, opts)
