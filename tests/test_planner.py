@@ -33,6 +33,32 @@ def test_exports_every_declared_symbol(M):
     assert set(M.EXPORTED) <= declared
 
 
+def test_null_arguments_are_rejected(M):
+    """Every compute entry point answers MHC_EINVAL to a NULL plan / batch / output before
+    touching the device (so the checks hold on a machine without a GPU), with a message."""
+    import ctypes
+    L = M.lib()
+    vp = ctypes.c_void_p
+    d = ctypes.c_double()
+    calls = {
+        "mhc_correlator": lambda: L.mhc_correlator(None, None, None, None, None, None),
+        "mhc_correlator_cw": lambda: L.mhc_correlator_cw(None, None, None, None, None, None, None, None),
+        "mhc_correlator_backward": lambda: L.mhc_correlator_backward(None, None, None, None, None, None, None,
+                                                                     None, None),
+        "mhc_correlator_noalloc": lambda: L.mhc_correlator_noalloc(None, None, None, None, None, None),
+        "mhc_pair_dets": lambda: L.mhc_pair_dets(None, None, ctypes.c_int64(1), None, None, None, None, None),
+        "mhc_get_status": lambda: L.mhc_get_status(None, None),
+        "mhc_plan_stats": lambda: L.mhc_plan_stats(None, None),
+        "mhc_batch_create": lambda: L.mhc_batch_create(None, 1, None),
+        "mhc_batch_correlator": lambda: L.mhc_batch_correlator(None, None, None, None),
+        "mhc_batch_info": lambda: L.mhc_batch_info(None, None, None),
+        "mhc_fp64_peak": lambda: L.mhc_fp64_peak(0, ctypes.byref(d), None),
+    }
+    for name, call in calls.items():
+        assert call() == M.MHC_EINVAL, name
+        assert L.mhc_last_error(), name
+
+
 def _walk(M, w, plan):
     """Evaluate every (member, sink) determinant from the plan's families: the shared rows
     of the reference tuple plus the member's rows (LAPACK det), times the member sign."""
