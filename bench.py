@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward comparison")
+    ap.add_argument("--workload", default="he4", choices=["he4", "large", "large_noforce", "large_small"],
+                    help="he4 (the benchmark line) or the n = 18 nucleus variants; the latter time "
+                         "the forward only (no adjoint, batch or CPU baseline)")
     ap.add_argument("--fp64-peak", action="store_true",
                     help="only measure the FP64 (DFMA) peak: >= 1 s of independent chains on every SM, "
                          "SM clocks sampled meanwhile")
@@ -62,10 +65,23 @@ def dist_env():
     return rank, world, local
 
 
-def workload(rank: int, scale: float = 1.0):
-    """The rank's own replica: the He-4-like workload on its own propagators (seed)."""
+def workload(rank: int, scale: float = 1.0, name: str = "he4"):
+    """The rank's own replica on its own propagators (seed).  he4: the He-4-like workload
+    of the benchmark line; large, large_noforce, large_small: the 32768 x 32768 n = 18
+    nucleus (10 % two-row families, 1 % forced near-singular members), the same without
+    the forced members, and a 1/8-scale copy of the first (for profiler captures)."""
     from paper_1411_3691_gb300 import workloads as wl
-    return wl.helium4(scale=scale, seed=1000 + 17 * rank)
+    if name == "he4":
+        return wl.helium4(scale=scale, seed=1000 + 17 * rank)
+    if name == "large":
+        return wl.large_nucleus(scale=scale, seed=3000 + 17 * rank)
+    if name == "large_small":
+        return wl.large_nucleus(scale=scale / 8, seed=3000 + 17 * rank)
+    if name == "large_noforce":
+        fams = [32] * max(1, int(round(1024 * scale)))
+        return wl.make_workload("large_noforce_n18_L96", [18, 18], [96, 96], fams, fams, diag=3.0,
+                                seed=3000 + 17 * rank, two_row_frac=0.1, forced_frac=0.0, twins=8)
+    raise ValueError(f"unknown workload {name}")
 
 
 def max_over_ranks(x: float, pg, device) -> float:
@@ -207,7 +223,9 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    w = workload(rank)
+    w = workload(rank, name=args.workload)
+    if args.workload != "he4":  # the nucleus variants time the forward only
+        args.no_adjoint = args.no_batch = args.no_cpu_baseline = True
     plan = mhc.Plan.from_workload(w)
     st = plan.stats()
     S = [torch.from_numpy(s).cuda() for s in w.S]
@@ -251,8 +269,10 @@ def run_gpu(args):
 
     # roofline of the forward kernel (FP64 ALU bound): algorithmic flops per launch over the
     # step's device time, against the FP64 peak measured above
+    # refactors are not counted (they run partly as shared factorisations of a group of
+    # pairs, below a fresh LU each): the FLOP figure is a lower bound of the work done
     refactor_pairs = (st["refactor_parent"] + st["refactor_child"]) / max(args.steps, 1)
-    flops = st["flops_per_call"] + refactor_pairs * st["fresh_lu_flops_per_pair"] / 2
+    flops = st["flops_per_call"]
     achieved = flops / (ms_per_step * 1e-3) / 1e12
     peak = peak_flops / 1e12
 
@@ -294,18 +314,21 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "flavours": 2, "n_f": 6, "L": 48, "n_src": len(w.w_src),
+            "config": {"workload": w.name, "flavours": len(w.n_f), "n_f": w.n_f[0], "L": w.L_f[0],
+                       "n_src": len(w.w_src),
                        "n_snk": len(w.w_snk), "pairs_per_gpu": pairs, "families": st["families"],
                        "parallelism": f"{world} independent correlators (one per GPU)",
                        "l2": "flushed between timed steps (256 MiB write outside the events)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": FWD_TRAFFIC_BYTES,
+                         "frac": achieved / peak,
+                         "traffic": FWD_TRAFFIC_BYTES if args.workload == "he4" else None,
                          "peak_source": "FP64 DFMA chains on all SMs, measured in this run "
                                         f"(nominal {NOMINAL_FP64_TFLOPS:.3f} from unit counts and clocks)",
                          "flops_per_step": flops},
             "e2e": {"value": whole_job_rate(world, pairs, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 16},
-            "gpu_launches": (3 if st["two_sided_blocks"] > 0 else 2) * args.steps,
+            # block factors (one launch, two when a flavour has n > 6), forward, reduction
+            "gpu_launches": ((1 + (max(w.n_f) > 6) if st["two_sided_blocks"] > 0 else 0) + 2) * args.steps,
             "clocks": clocks,
             "refactors_per_step": refactor_pairs,
             "adjoint": adjoint,
