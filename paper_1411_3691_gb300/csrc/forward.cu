@@ -47,6 +47,28 @@ size_t forward_smem_bytes(int slots, int tile) {
   return cache + queue;
 }
 
+// fwd_kernel over items [0, items): with a narrow-first order, the rank-1 families in a
+// launch with the compact y cache, then the others with the wide one (smem: its size).
+static cudaError_t launch_fwd_items(const FwdArgs& a, int ncmax, int tile, int64_t items, size_t smem,
+                                    cudaStream_t s) {
+  auto one = [&](const FwdArgs& x, int64_t count, size_t bytes) {
+    return ncmax <= 8 ? launch_fwd_nc8(x, tile, count, bytes, s)
+                      : (ncmax <= 18 ? launch_fwd_nc18(x, tile, count, bytes, s)
+                                     : launch_fwd_nc32(x, tile, count, bytes, s));
+  };
+  const int64_t nn = a.fam_order ? a.n_narrow * a.n_tiles : 0;
+  if (nn <= 0 || nn >= items) return one(a, items, smem);
+  FwdArgs an = a;
+  an.slots = a.slots_n;
+  for (int f = 0; f < MHC_FMAX; f++) an.yoff[f] = a.yoff_n[f];
+  an.item0 = 0;
+  cudaError_t e = one(an, nn, forward_smem_bytes(a.slots_n, tile));
+  if (e != cudaSuccess) return e;
+  FwdArgs aw = a;
+  aw.item0 = nn;
+  return one(aw, items - nn, smem);
+}
+
 cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,
                            size_t smem, double* out, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
@@ -59,13 +81,7 @@ cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam,
       e = launch_kfac_nc32(a, n_fam, s);
     if (e != cudaSuccess) return e;
   }
-  if (ncmax <= 8)
-    e = launch_fwd_nc8(a, tile, items, smem, s);
-  else if (ncmax <= 18)
-    e = launch_fwd_nc18(a, tile, items, smem, s);
-  else
-    e = launch_fwd_nc32(a, tile, items, smem, s);
-  if (e != cudaSuccess) return e;
+  if ((e = launch_fwd_items(a, ncmax, tile, items, smem, s)) != cudaSuccess) return e;
   return launch_reduce(a.partials, items, out, s);
 }
 
@@ -82,9 +98,7 @@ cudaError_t launch_forward_cw(const FwdArgs& a0, const double* const* ws, const 
     FwdArgs a = a0;
     a.w_src = ws[k >> 1];
     a.w_snk = wk[k & 1];
-    e = ncmax <= 8 ? launch_fwd_nc8(a, tile, items, smem, s)
-                   : (ncmax <= 18 ? launch_fwd_nc18(a, tile, items, smem, s) : launch_fwd_nc32(a, tile, items, smem, s));
-    if (e != cudaSuccess) return e;
+    if ((e = launch_fwd_items(a, ncmax, tile, items, smem, s)) != cudaSuccess) return e;
     if ((e = launch_reduce(a.partials, items, tmp + 2 * k, s)) != cudaSuccess) return e;
   }
   combine_cw<<<1, 32, 0, s>>>(tmp, out);

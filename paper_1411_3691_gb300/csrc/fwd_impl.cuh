@@ -119,19 +119,16 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
   return parity ? dev::cneg(det) : det;
 }
 
-// Refactor the queued pairs: the lane's product of the flavours that passed, times fresh
-// determinants of the flavours that failed.  Pairs that share a member and a two-sided
-// sink family (one changed column, rank-1 family) are factorised together (group_fresh);
-// the others one per lane.  Called by the whole warp.
+// Refactor one pair per lane (the lanes with have; e: the pair, j: its sink position):
+// the product of the flavours that passed, times fresh determinants of the flavours that
+// failed, accumulated into acc.  Pairs that share a member and a two-sided sink family
+// (one changed column, rank-1 family) are factorised together (group_fresh); the others
+// one per lane.  Called by the whole warp.
 template <int NCMAX>
-__device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
+__device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& e, int64_t j,
                               double2& acc) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const bool have = lane < count;
-  QEntry e = {};
-  if (have) e = q[lane];
-  const int64_t j = jbase + (have ? e.lane : 0);
   const int32_t* cols = dev::sink_cols(a, j);
   double2 prod = have ? e.prod : make_double2(1.0, 0.0);
   const int Q = a.snk_orig ? a.snk_q[j] : -1;
@@ -161,6 +158,17 @@ __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int
     acc.x = fma(e.w, prod.x, acc.x);
     acc.y = fma(e.w, prod.y, acc.y);
   }
+}
+
+// Refactor the first count queued pairs (one per lane).  Called by the whole warp.
+template <int NCMAX>
+__device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
+                              double2& acc) {
+  const int lane = threadIdx.x & 31;
+  const bool have = lane < count;
+  QEntry e = {};
+  if (have) e = q[lane];
+  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), acc);
 }
 
 // One work item (family W x sink tile) by the whole thread block; the block's sum goes
@@ -242,7 +250,22 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       acc.y = fma(w, prod.y, acc.y);
     }
     const unsigned ball = __ballot_sync(0xffffffffu, need);
-    if (ball) {
+    if (ball == 0xffffffffu) {
+      // every lane refactors this member (a member near-singular against its family): the
+      // pairs go straight to the refactor as one group, past the queue, so that a queue
+      // flush never splits the group that group_fresh factorises once
+      QEntry e;
+      e.member = m;
+      e.lane = lane;
+      e.fail = (int32_t)fail;
+      e.pad = 0;
+      e.prod = prod;
+      e.w = w;
+      e.pad2 = 0.0;
+      process_pairs<NCMAX>(a, W, true, e, j, acc);
+      n_parent += __popc(fail & pguard);
+      n_child += __popc(fail & ~pguard);
+    } else if (ball) {
       if (need) {
         const int pos = qn + __popc(ball & ((1u << lane) - 1u));
         QEntry e;
@@ -298,8 +321,10 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
 template <int NCMAX>
 __global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
   extern __shared__ double2 smem[];
-  const int64_t item = blockIdx.x;
-  fwd_item<NCMAX>(a, (int)(item / a.n_tiles), (int)(item % a.n_tiles), smem, &a.partials[item]);
+  const int64_t item = a.item0 + blockIdx.x;
+  const int64_t pos = item / a.n_tiles;
+  const int W = a.fam_order ? a.fam_order[pos] : (int)pos;
+  fwd_item<NCMAX>(a, W, (int)(item % a.n_tiles), smem, &a.partials[item]);
 }
 
 // Per-pair determinants through the same update path (one thread per pair).

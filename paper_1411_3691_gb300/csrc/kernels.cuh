@@ -49,6 +49,15 @@ struct FwdArgs {
   int64_t n_q;
   int kstride;
   int koff[MHC_FMAX];
+  // narrow-first work order of fwd_kernel: the families whose flavours all have rank 1
+  // (n_narrow of them) come first and run in a launch of their own with the compact y cache
+  // (yoff_n, slots_n: n slots per flavour), so that more blocks fit on an SM; the others
+  // follow with the wide cache (yoff, slots).  fam_order == nullptr: natural order, one
+  // launch.
+  const int32_t* fam_order;  // [n_fam] family at each work position
+  int64_t item0;             // first work item of the launch
+  int64_t n_narrow;
+  int slots_n, yoff_n[MHC_FMAX];
 };
 
 namespace dev {

@@ -40,7 +40,7 @@ mhc_status upload(T** dst, const T* src, size_t count) {
 }
 
 void free_device(DevicePlan& d) {
-  void* ptrs[] = {d.fam_info, d.fam_rank, d.fam_arow, d.mem_term, d.mem_par, d.mem_lab,
+  void* ptrs[] = {d.fam_info, d.fam_rank, d.fam_arow, d.fam_order, d.mem_term, d.mem_par, d.mem_lab,
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
                   d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard, d.kinv, d.bwd_stage,
@@ -111,6 +111,27 @@ mhc_status ensure_device(Plan& p) {
   if ((st = upload(&d.fam_info, info.data(), info.size())) != MHC_OK) return st;
   if ((st = upload(&d.fam_rank, p.fam_rank.data(), p.fam_rank.size())) != MHC_OK) return st;
   if ((st = upload(&d.fam_arow, p.fam_arow.data(), p.fam_arow.size())) != MHC_OK) return st;
+  // narrow-first work order when both kinds of family occur and the compact y cache is
+  // smaller: the rank-1 families first, each kind in plan order
+  {
+    std::vector<int32_t> order;
+    order.reserve(p.n_fam);
+    for (int pass = 0; pass < 2; pass++)
+      for (int64_t W = 0; W < p.n_fam; W++) {
+        bool narrow = true;
+        for (int f = 0; f < F; f++) narrow = narrow && p.fam_rank[W * F + f] <= 1;
+        if (narrow == (pass == 0)) order.push_back((int32_t)W);
+        if (pass == 0 && W == p.n_fam - 1) d.n_narrow = (int64_t)order.size();
+      }
+    int yw[MHC_FMAX], sw = 0, sn = 0;
+    plan_slots(p, yw, &sw);
+    for (int f = 0; f < F; f++) sn += p.n_f[f];
+    if (d.n_narrow > 0 && d.n_narrow < p.n_fam && sn < sw) {
+      if ((st = upload(&d.fam_order, order.data(), order.size())) != MHC_OK) return st;
+    } else {
+      d.n_narrow = 0;
+    }
+  }
   if ((st = upload(&d.mem_term, term.data(), term.size())) != MHC_OK) return st;
   if ((st = upload(&d.mem_par, p.mem_par.data(), p.mem_par.size())) != MHC_OK) return st;
   if ((st = upload(&d.mem_lab, p.mem_lab.data(), p.mem_lab.size())) != MHC_OK) return st;
@@ -178,6 +199,13 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
   a.w_snk = w_snk ? w_snk : p.dev.w_snk;
   a.partials = reinterpret_cast<double2*>(p.dev.partials);
   a.counters = p.dev.counters;
+  a.fam_order = p.dev.fam_order;
+  a.n_narrow = p.dev.n_narrow;
+  for (int f = 0; f < p.F; f++) {
+    a.yoff_n[f] = a.slots_n;
+    a.slots_n += p.n_f[f];
+  }
+  a.slots_n = std::max(a.slots_n, 1);
   if (p.dev.two_sided) {
     a.snk_pos = p.dev.snk_lab2;
     a.snk_orig = p.dev.snk_order;
