@@ -28,26 +28,29 @@ struct QEntry {
 };
 
 // Fresh determinants of a group of queued pairs that share member m and a two-sided sink
-// family Q with one changed column (flavour f, rank-1 family): their matrices agree in the
-// first n - 1 columns (the family's shared rows and member row against the sink family's
-// shared columns) and differ in the last.  Partial-pivot LU eliminates column by column, so
+// family Q with one changed column (flavour f; family of rank rho): their matrices agree in
+// the first n - 1 columns (the family's n - rho shared rows and the member's rho rows, in
+// member_rows order, against the sink family's shared columns) and differ in the last.  Partial-pivot LU eliminates column by column, so
 // the pivots and multipliers of the first n - 1 columns are common to the group: the warp
 // factorises them once (lane i holds row i), then every lane of the group carries its own
 // sink's last column through the same steps -- the arithmetic of a fresh LU per pair at
 // O(n^2) per pair instead of O(n^3).  Called by the whole warp; returns the determinant on
 // the lanes in grp.
 template <int NC>
-__device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, int m, int Q, int64_t j,
-                                               unsigned grp) {
+__device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, int rho, int m, int Q,
+                                               int64_t j, unsigned grp) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int n = a.n_f[f];
   const int L = a.L_f[f];
   const dev::cd* S = a.S[f];
   const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+  const int32_t* mlab = a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK;
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
-  // lane i < n: row i of the n x (n - 1) block (rows: shared rows, then the member's row)
-  const int rlab = lane < n - 1 ? arow[lane] : a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK];
+  // label of row i: the family's shared rows, then the member's changed rows
+  auto row_label = [&](int i) { return i < n - rho ? arow[i] : mlab[min(i - (n - rho), rho - 1)]; };
+  // lane i < n: row i of the n x (n - 1) block
+  const int rlab = row_label(lane);
   dev::cd R[NC];
 #pragma unroll
   for (int u = 0; u < NC - 1; u++)
@@ -58,8 +61,7 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
   const int lc = mine ? dev::sink_cols(a, j)[a.off_f[f] + n - 1] : 0;
 #pragma unroll
   for (int i = 0; i < NC; i++) {
-    const int li = i < n - 1 ? arow[i < n - 1 ? i : 0] : a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK];
-    c[i] = (mine && i < n) ? dev::ldS(S + (size_t)li * L + lc) : make_double2(0.0, 0.0);
+    c[i] = (mine && i < n) ? dev::ldS(S + (size_t)row_label(i) * L + lc) : make_double2(0.0, 0.0);
   }
   unsigned piv = 0;  // rows already used as pivots
   int parity = 0;
@@ -136,20 +138,21 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
   for (int f = 0; f < a.F; f++) {
     const bool need = have && ((e.fail >> f) & 1);
     const int n = a.n_f[f];
-    const bool grouped = need && NCMAX <= 18 && n >= 2 && a.fam_rank[(int64_t)W * a.F + f] == 1 && Q >= 0 &&
-                         a.q_two[Q] && a.q_rank[(int64_t)Q * a.F + f] == 1;
+    const int rho = a.fam_rank[(int64_t)W * a.F + f];
+    const bool grouped = need && NCMAX <= 18 && n >= 2 && Q >= 0 && a.q_two[Q] &&
+                         a.q_rank[(int64_t)Q * a.F + f] == 1;
     unsigned todo = __ballot_sync(FULL, grouped);
     while (todo) {
       const int leader = __ffs(todo) - 1;
       const int lm = __shfl_sync(FULL, have ? e.member : 0, leader);
       const int lq = __shfl_sync(FULL, Q, leader);
       const unsigned grp = __ballot_sync(FULL, ((todo >> lane) & 1) && e.member == lm && Q == lq);
-      const double2 d = group_fresh<NCMAX <= 18 ? NCMAX : 18>(a, W, f, lm, lq, j, grp);
+      const double2 d = group_fresh<NCMAX <= 18 ? NCMAX : 18>(a, W, f, rho, lm, lq, j, grp);
       if ((grp >> lane) & 1) prod = dev::cmul(prod, d);
       todo &= ~grp;
     }
     if (need && !grouped) {
-      dev::member_rows(a, W, e.member, f, a.fam_rank[(int64_t)W * a.F + f], rows);
+      dev::member_rows(a, W, e.member, f, rho, rows);
       const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, cols + a.off_f[f]);
       prod = dev::cmul(prod, d);
     }

@@ -243,3 +243,28 @@ def test_three_row_families(M, one_sided):
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
     ii, jj = np.meshgrid(np.arange(len(w.w_src)), np.arange(len(w.w_snk)), indexing="ij")
     check_pairs(M, w, plan, S, ii.ravel(), jj.ravel())
+
+
+@pytest.mark.parametrize("three_row_frac", [0.0, 0.3])
+def test_forced_members_in_multi_row_families(M, three_row_frac):
+    """Members near-singular against families with two (three) changed rows: whole warps of
+    their pairs fail the guard and are refactored as groups that share the member's rows and
+    the sink family's shared columns (Sec. 2.1's fallback to a fresh factorisation); C against
+    the oracle, and the refactors counted."""
+    w = wl.make_workload("forced_multirow", [14, 12], [64, 56], [32, 32, 32], [32, 32, 32, 7], seed=71,
+                         two_row_frac=0.5, three_row_frac=three_row_frac, forced_frac=0.2, twins=8)
+    info = w.meta["src"]
+    forced = info["forced"]
+    assert any(len(info["rows"][info["family_of"][t]][f]) >= 2 for t, f in forced)
+    opts = M.default_opts()
+    opts.rank3 = 1 if three_row_frac else 0
+    C, plan, S = gpu_C(M, w, opts)
+    st = plan.stats()
+    assert st["rank2_family_flavours"] > 0
+    if three_row_frac:
+        assert st["rank3_family_flavours"] > 0
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    assert plan.stats()["refactor_child"] >= len(forced) * len(w.w_snk) // 2
+    plan.close()
