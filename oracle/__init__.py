@@ -34,13 +34,16 @@ _lock = threading.Lock()
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _f64p = ctypes.POINTER(ctypes.c_double)
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_mhc_oracle.so (gcc, no arch-specific flags)."""
+    """Compile the oracle into oracle/_mhc_oracle.so (gcc, no arch-specific flags; no
+    contraction of a*b+c into fused multiply-adds, which gcc does by default on some targets,
+    so that the oracle rounds the same way on every host)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -78,7 +81,7 @@ def _load():
 def build_mutant(k: int, out_dir: str) -> str:
     """Compile the oracle with planted mistake number k (mutation test of the pins)."""
     path = os.path.join(out_dir, f"_mhc_oracle_mutant{k}.so")
-    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", f"-DORACLE_MUTANT={k}", "-o", path, _SRC, "-lm"])
+    subprocess.check_call(["gcc", *_CFLAGS, f"-DORACLE_MUTANT={k}", "-o", path, _SRC, "-lm"])
     return path
 
 

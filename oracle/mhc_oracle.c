@@ -69,6 +69,15 @@ static double neu_value(const neumaier* a) { return a->s + a->c; }
 
 static double abs1(cplx z) { return fabs(creal(z)) + fabs(cimag(z)); }
 
+/* a / b written out as a conj(b) / |b|^2, so that b / b is exactly 1 on every host (the C
+ * library's complex division is not exact there on all targets); the entries of S are
+ * of order one, far from overflow. */
+static cplx cdiv(cplx a, cplx b) {
+  const double br = creal(b), bi = cimag(b), ar = creal(a), ai = cimag(a);
+  const double d = br * br + bi * bi;
+  return CMPLX((ar * br + ai * bi) / d, (ai * br - ar * bi) / d);
+}
+
 /* ---------------------------------------------------------------------------------- */
 /* Determinant by LU with partial pivoting (Sec. 2, first paragraph).                   */
 /* A is n x n row-major and is overwritten by the factors.                              */
@@ -102,7 +111,7 @@ static cplx lu_det(int n, cplx* A) {
 #endif
     det *= piv;
     for (int i = k + 1; i < n; i++) {
-      cplx l = A[i * n + k] / piv;
+      cplx l = cdiv(A[i * n + k], piv);
       A[i * n + k] = l;
       for (int j = k + 1; j < n; j++) A[i * n + j] -= l * A[k * n + j];
     }
@@ -497,7 +506,7 @@ double oracle_cond_inf(int n, const double* G_in) {
       perm[p] = t;
     }
     for (int i = k + 1; i < n; i++) {
-      cplx l = A[i * n + k] / A[k * n + k];
+      cplx l = cdiv(A[i * n + k], A[k * n + k]);
       A[i * n + k] = l;
       for (int j = k + 1; j < n; j++) A[i * n + j] -= l * A[k * n + j];
     }
@@ -510,7 +519,7 @@ double oracle_cond_inf(int n, const double* G_in) {
       for (int k = 0; k < m; k++) z[m] -= A[m * n + k] * z[k];
     for (int m = n - 1; m >= 0; m--) {
       for (int k = m + 1; k < n; k++) z[m] -= A[m * n + k] * z[k];
-      z[m] /= A[m * n + m];
+      z[m] = cdiv(z[m], A[m * n + m]);
     }
     for (int m = 0; m < n; m++) X[m * n + c] = z[m];
   }
