@@ -20,6 +20,8 @@
 // per-warp accumulators are summed in a fixed order by finalize kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace mhc {
@@ -629,12 +631,17 @@ __device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArg
 #undef MHC_COF
 }
 
-// Scatter of one warp's 32 sinks into its accumulator rows (flavour f).  Lane s owns row
-// s: a shared row (s < n - 1, values from the staged cofactor block) or member s - n + 1
-// (gamma times the cached y).  Within a two-sided sink family the shared columns carry the
-// same labels for every sink, so their contributions are summed in registers and added to
-// the row once per family; the changed columns are added per sink.  Fixed order: no two
-// lanes touch the same row, and every lane walks the sinks and columns in order.  Each
+// Scatter of one warp's 32 sinks into its accumulator rows (flavour f).  The cells of the
+// block -- row s (a shared row, s < n - 1, values from the staged cofactor block, or member
+// s - n + 1, gamma times the cached y) by column q -- are dealt to the lanes 32 at a time,
+// the members' cells column by column, then the shared rows' cells, cell e to lane e mod
+// 32, so that the lanes stay busy whatever the number of rows, the lanes of one step
+// mostly read one column of y, and a step of shared rows only adds (gamma = 1).  Within a two-sided sink family the shared columns carry the same labels for every
+// sink, so their contributions are summed in registers and added to the row once per
+// family; the changed columns are added per sink.  Lanes that hold cells of one row add to
+// distinct labels (the columns of a sink carry distinct labels), except for a sink that
+// repeats a label, whose cells are added one column at a time; a __syncwarp after every
+// sink orders the additions to one accumulator entry by sink, so the order is fixed.  Each
 // sink's metadata (sink family, number of shared columns, column labels, weight) sits in
 // the registers of the sink's own lane and reaches the other lanes by shuffles.
 template <int NC, int NFIX>
@@ -648,63 +655,92 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
   const int n = NFIX ? NFIX : n_rt;
   const int M = n - 1;
   const int nslots = M + kW;
+  const int ncells = nslots * n;
   int cl[NC];
 #pragma unroll UNR
   for (int q = 0; q < n; q++) cl[q] = mycol[q];
-  for (int s = lane; s < ((nslots + 31) & ~31); s += 32) {
-    const bool act = s < nslots;
+  // does this lane's sink repeat a label in flavour f
+  int myrep = 0;
+#pragma unroll UNR
+  for (int q = 1; q < n; q++)
+#pragma unroll UNR
+    for (int p = 0; p < q; p++) myrep |= cl[q] == cl[p];
+  for (int e0 = 0; e0 < ncells; e0 += 32) {
+    const int e = e0 + lane;
+    const bool act = e < ncells;
+    // member cells first (column by column), then the shared rows' cells
+    const int nmc = kW * n;
+    const bool shround = e0 >= nmc;  // every cell of this step is a shared row's: g = 1
+    const int e1 = e - nmc;
+    const int q = !act ? 0 : (e < nmc ? e / kW : e1 / M);
+    const int s = !act ? 0 : (e < nmc ? M + (e - q * kW) : e1 - q * M);
     const bool mem = s >= M;
-    const int c = act && mem ? s - M : 0;
-    cd* Drow = Df + (size_t)(act ? s : 0) * B.Lmax;
-    cd acc[NC];
-    int curlab[NC];
-    int curQ = -2, nsh = 0;
+    const int c = mem ? s - M : 0;
+    cd* Drow = Df + (size_t)s * B.Lmax;
+    const cd* Ycol = Ysm + (size_t)(a.yoff[f] + q) * T;
+    // the sweep over the sinks, compiled apart for the steps of shared rows only
+    auto sweep = [&](auto sh) {
+      cd acc = make_double2(0.0, 0.0);
+      int curlab = 0, curQ = -2, nsh = 0;
+      for (int jl = 0; jl <= nlive; jl++) {
+        const bool live = jl < nlive;
+        const int src = jl & 31;
+        const int Qj = __shfl_sync(FULL, myQ, src);
+        const int nsj = __shfl_sync(FULL, mynsh, src);
+        const int rep = __shfl_sync(FULL, myrep, src);
+        int lab = 0;  // the label of this cell's column in sink jl
 #pragma unroll UNR
-    for (int q = 0; q < n; q++) {
-      acc[q] = make_double2(0.0, 0.0);
-      curlab[q] = 0;
-    }
-    for (int jl = 0; jl <= nlive; jl++) {
-      const bool live = jl < nlive;
-      const int src = jl & 31;
-      const int Qj = __shfl_sync(FULL, myQ, src);
-      const int nsj = __shfl_sync(FULL, mynsh, src);
-      int cj[NC];
-#pragma unroll UNR
-      for (int q = 0; q < n; q++) cj[q] = __shfl_sync(FULL, cl[q], src);
-      if (!live || Qj != curQ || Qj < 0) {  // flush the summed shared columns of the previous family
-        if (act) {
-#pragma unroll UNR
-          for (int q = 0; q < n; q++)
-            if (q < nsh) {
-              cd& d = Drow[curlab[q]];
-              d.x += acc[q].x;
-              d.y += acc[q].y;
+        for (int p = 0; p < n; p++) {
+          const int t = __shfl_sync(FULL, cl[p], src);
+          lab = p == q ? t : lab;
+        }
+        if (!live || Qj != curQ || Qj < 0) {  // flush the summed shared columns of the previous family
+          // one column at a time: the family's shared labels may repeat
+          for (int p = 0; p < nsh; p++) {
+            if (act && q == p) {
+              cd& d = Drow[curlab];
+              d.x += acc.x;
+              d.y += acc.y;
             }
+            __syncwarp();
+          }
+          if (!live) break;
+          curQ = Qj;
+          nsh = nsj;
+          acc = make_double2(0.0, 0.0);
+          curlab = lab;
         }
-        if (!live) break;
-        curQ = Qj;
-        nsh = nsj;
-#pragma unroll UNR
-        for (int q = 0; q < n; q++) {
-          acc[q] = make_double2(0.0, 0.0);
-          curlab[q] = cj[q];
+        const int ts = warp * 32 + jl;
+        const cd g = (mem && !decltype(sh)::value) ? Dets[dix(c, f, B.kmax, T, ts)] : make_double2(1.0, 0.0);
+        const cd v = mem ? Ycol[ts] : Stage[(size_t)ts * B.mn_max + s * n + q];
+        const bool shcol = q < nsh;
+        if (!rep) {
+          // one complex FMA (an addition in a step of shared rows) per lane, on the register
+          // sum or on the accumulator entry
+          const cd base = shcol ? acc : (act ? Drow[lab] : make_double2(0.0, 0.0));
+          cd r;
+        if constexpr (decltype(sh)::value)
+          r = dev::cadd(base, v);
+        else
+          r = dev::cfma(g, v, base);
+          if (shcol)
+            acc = r;
+          else if (act)
+            Drow[lab] = r;
+        } else {
+          if (shcol) acc = dev::cfma(g, v, acc);
+          for (int p = nsh; p < n; p++) {
+            if (act && q == p) Drow[lab] = dev::cfma(g, v, Drow[lab]);
+            __syncwarp();
+          }
         }
+        __syncwarp();
       }
-      const int ts = warp * 32 + jl;
-      const cd g = mem ? Dets[dix(c, f, B.kmax, T, ts)] : make_double2(1.0, 0.0);
-      const cd* st = Stage + (size_t)ts * B.mn_max + (mem ? 0 : s * n);
-#pragma unroll UNR
-      for (int q = 0; q < n; q++) {
-        const cd v = mem ? Ysm[(size_t)(a.yoff[f] + q) * T + ts] : st[q];
-        if (q < nsh) {
-          acc[q] = dev::cfma(g, v, acc[q]);
-        } else if (act) {
-          cd& d = Drow[cj[q]];
-          d = dev::cfma(g, v, d);
-        }
-      }
-    }
+    };
+    if (shround)
+      sweep(std::true_type{});
+    else
+      sweep(std::false_type{});
   }
 }
 
