@@ -84,6 +84,18 @@ def workload(rank: int, scale: float = 1.0, name: str = "he4"):
     raise ValueError(f"unknown workload {name}")
 
 
+def forward_launches(plan, w, st) -> int:
+    """Kernel launches of one forward call: the block factors of a two-sided plan (one
+    launch, two when a flavour has n > 6), fwd_kernel once per group of families that share
+    a y-cache layout (the rank of each flavour; one launch when all share one, at most
+    four), and the reduction."""
+    keys = {tuple(max(1, int(r)) if n > 0 else 0 for r, n in zip(row, w.n_f))
+            for row in plan.families()["rank"]}
+    fwd = 1 if len(keys) < 2 else min(len(keys), 4)
+    kfac = (1 + (max(w.n_f) > 6)) if st["two_sided_blocks"] > 0 else 0
+    return kfac + fwd + 1
+
+
 def max_over_ranks(x: float, pg, device) -> float:
     """The slowest rank's time: every rank gets the maximum (all-reduce MAX)."""
     if pg is None:
@@ -327,8 +339,7 @@ def run_gpu(args):
                          "flops_per_step": flops},
             "e2e": {"value": whole_job_rate(world, pairs, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 16},
-            # block factors (one launch, two when a flavour has n > 6), forward, reduction
-            "gpu_launches": ((1 + (max(w.n_f) > 6) if st["two_sided_blocks"] > 0 else 0) + 2) * args.steps,
+            "gpu_launches": forward_launches(plan, w, st) * args.steps,
             "clocks": clocks,
             "refactors_per_step": refactor_pairs,
             "adjoint": adjoint,

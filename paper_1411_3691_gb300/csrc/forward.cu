@@ -47,8 +47,8 @@ size_t forward_smem_bytes(int slots, int tile) {
   return cache + queue;
 }
 
-// fwd_kernel over items [0, items): with a narrow-first order, the rank-1 families in a
-// launch with the compact y cache, then the others with the wide one (smem: its size).
+// fwd_kernel over items [0, items): one launch per layout range, each with its own y
+// cache, or one launch with the plan's layout (smem: its size).
 static cudaError_t launch_fwd_items(const FwdArgs& a, int ncmax, int tile, int64_t items, size_t smem,
                                     cudaStream_t s) {
   auto one = [&](const FwdArgs& x, int64_t count, size_t bytes) {
@@ -56,17 +56,18 @@ static cudaError_t launch_fwd_items(const FwdArgs& a, int ncmax, int tile, int64
                       : (ncmax <= 18 ? launch_fwd_nc18(x, tile, count, bytes, s)
                                      : launch_fwd_nc32(x, tile, count, bytes, s));
   };
-  const int64_t nn = a.fam_order ? a.n_narrow * a.n_tiles : 0;
-  if (nn <= 0 || nn >= items) return one(a, items, smem);
-  FwdArgs an = a;
-  an.slots = a.slots_n;
-  for (int f = 0; f < MHC_FMAX; f++) an.yoff[f] = a.yoff_n[f];
-  an.item0 = 0;
-  cudaError_t e = one(an, nn, forward_smem_bytes(a.slots_n, tile));
-  if (e != cudaSuccess) return e;
-  FwdArgs aw = a;
-  aw.item0 = nn;
-  return one(aw, items - nn, smem);
+  if (!a.fam_order || a.n_ranges <= 0) return one(a, items, smem);
+  for (int r = 0; r < a.n_ranges; r++) {
+    const FwdRange& g = a.ranges[r];
+    if (g.count <= 0) continue;
+    FwdArgs ar = a;
+    ar.slots = g.slots;
+    for (int f = 0; f < MHC_FMAX; f++) ar.yoff[f] = g.yoff[f];
+    ar.item0 = g.first * a.n_tiles;
+    const cudaError_t e = one(ar, g.count * a.n_tiles, forward_smem_bytes(g.slots, tile));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,

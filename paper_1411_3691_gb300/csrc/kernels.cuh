@@ -7,6 +7,7 @@
 
 #include "../../include/mhc.h"
 #include "device.cuh"
+#include "layout.h"
 
 namespace mhc {
 
@@ -49,15 +50,15 @@ struct FwdArgs {
   int64_t n_q;
   int kstride;
   int koff[MHC_FMAX];
-  // narrow-first work order of fwd_kernel: the families whose flavours all have rank 1
-  // (n_narrow of them) come first and run in a launch of their own with the compact y cache
-  // (yoff_n, slots_n: n slots per flavour), so that more blocks fit on an SM; the others
-  // follow with the wide cache (yoff, slots).  fam_order == nullptr: natural order, one
-  // launch.
+  // work order of fwd_kernel by y-cache layout: the families are grouped by the rank of
+  // each flavour (n slots for rank 1, r n + 1 for rank r >= 2), the all-rank-1 group first,
+  // and each group runs in a launch of its own with a cache sized for it, so that more
+  // blocks fit on an SM.  Range r covers work positions [first, first + count) with layout
+  // (yoff, slots); fam_order == nullptr: natural order, one launch with the plan's layout.
   const int32_t* fam_order;  // [n_fam] family at each work position
   int64_t item0;             // first work item of the launch
-  int64_t n_narrow;
-  int slots_n, yoff_n[MHC_FMAX];
+  int n_ranges;
+  FwdRange ranges[kMaxFwdRanges];
 };
 
 namespace dev {

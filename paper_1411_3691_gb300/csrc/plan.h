@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mhc.h"
+#include "layout.h"
 
 namespace mhc {
 
@@ -26,8 +27,9 @@ struct DevicePlan {
   int32_t* fam_info = nullptr;   // [W][4]: member offset, member count, pad, pad
   int32_t* fam_rank = nullptr;   // [W][F]
   int32_t* fam_arow = nullptr;   // [W][Tn]: shared-row labels first, then unused
-  int32_t* fam_order = nullptr;  // [W] rank-1 families first (see FwdArgs::fam_order), or nullptr
-  int64_t n_narrow = 0;          // families in the rank-1 launch
+  int32_t* fam_order = nullptr;  // [W] families grouped by y-cache layout (FwdArgs::fam_order), or nullptr
+  int n_ranges = 0;              // layout ranges of fam_order (FwdArgs::ranges)
+  FwdRange ranges[kMaxFwdRanges] = {};
   int32_t* mem_term = nullptr;   // [n_src] source term index of each member
   int32_t* mem_par = nullptr;    // [n_src] bit f: sign parity of flavour f
   int32_t* mem_lab = nullptr;    // [n_src][F][MHC_MAX_RANK]

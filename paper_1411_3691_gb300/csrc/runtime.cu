@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -111,25 +112,54 @@ mhc_status ensure_device(Plan& p) {
   if ((st = upload(&d.fam_info, info.data(), info.size())) != MHC_OK) return st;
   if ((st = upload(&d.fam_rank, p.fam_rank.data(), p.fam_rank.size())) != MHC_OK) return st;
   if ((st = upload(&d.fam_arow, p.fam_arow.data(), p.fam_arow.size())) != MHC_OK) return st;
-  // narrow-first work order when both kinds of family occur and the compact y cache is
-  // smaller: the rank-1 families first, each kind in plan order
+  // work order by y-cache layout (see FwdArgs::fam_order): families grouped by the rank of
+  // each flavour, each group in plan order, the groups by cache size (the all-rank-1 group
+  // first); beyond kMaxFwdRanges groups the largest layouts share the plan's layout, which
+  // holds any family.  One group: natural order, one launch.
   {
-    std::vector<int32_t> order;
-    order.reserve(p.n_fam);
-    for (int pass = 0; pass < 2; pass++)
-      for (int64_t W = 0; W < p.n_fam; W++) {
-        bool narrow = true;
-        for (int f = 0; f < F; f++) narrow = narrow && p.fam_rank[W * F + f] <= 1;
-        if (narrow == (pass == 0)) order.push_back((int32_t)W);
-        if (pass == 0 && W == p.n_fam - 1) d.n_narrow = (int64_t)order.size();
+    std::map<std::vector<int>, std::vector<int32_t>> groups;
+    for (int64_t W = 0; W < p.n_fam; W++) {
+      std::vector<int> key(F);
+      for (int f = 0; f < F; f++) key[f] = p.n_f[f] > 0 ? std::max(1, (int)p.fam_rank[W * F + f]) : 0;
+      groups[key].push_back((int32_t)W);
+    }
+    struct G {
+      int slots;
+      std::vector<int> yoff;
+      const std::vector<int32_t>* fams;
+    };
+    std::vector<G> gs;
+    for (auto& kv : groups) {
+      G g{0, std::vector<int>(F, 0), &kv.second};
+      for (int f = 0; f < F; f++) {
+        g.yoff[f] = g.slots;
+        const int r = kv.first[f], n = p.n_f[f];
+        g.slots += r >= 2 ? r * n + 1 : n;
       }
-    int yw[MHC_FMAX], sw = 0, sn = 0;
-    plan_slots(p, yw, &sw);
-    for (int f = 0; f < F; f++) sn += p.n_f[f];
-    if (d.n_narrow > 0 && d.n_narrow < p.n_fam && sn < sw) {
+      g.slots = std::max(g.slots, 1);
+      gs.push_back(std::move(g));
+    }
+    std::stable_sort(gs.begin(), gs.end(), [](const G& x, const G& y) { return x.slots < y.slots; });
+    d.n_ranges = 0;
+    if (gs.size() >= 2) {
+      int yw[MHC_FMAX], sw = 0;
+      plan_slots(p, yw, &sw);
+      std::vector<int32_t> order;
+      order.reserve(p.n_fam);
+      for (size_t k = 0; k < gs.size(); k++) {
+        const bool merged = k + 1 >= (size_t)kMaxFwdRanges;  // the last range takes the rest
+        FwdRange& r = d.ranges[d.n_ranges];
+        if (!merged || k + 1 == (size_t)kMaxFwdRanges) {
+          r.first = (int64_t)order.size();
+          r.count = 0;
+          r.slots = merged ? sw : gs[k].slots;
+          for (int f = 0; f < MHC_FMAX; f++) r.yoff[f] = f < F ? (merged ? yw[f] : gs[k].yoff[f]) : 0;
+          d.n_ranges++;
+        }
+        order.insert(order.end(), gs[k].fams->begin(), gs[k].fams->end());
+        d.ranges[d.n_ranges - 1].count += (int64_t)gs[k].fams->size();
+      }
       if ((st = upload(&d.fam_order, order.data(), order.size())) != MHC_OK) return st;
-    } else {
-      d.n_narrow = 0;
     }
   }
   if ((st = upload(&d.mem_term, term.data(), term.size())) != MHC_OK) return st;
@@ -200,12 +230,8 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
   a.partials = reinterpret_cast<double2*>(p.dev.partials);
   a.counters = p.dev.counters;
   a.fam_order = p.dev.fam_order;
-  a.n_narrow = p.dev.n_narrow;
-  for (int f = 0; f < p.F; f++) {
-    a.yoff_n[f] = a.slots_n;
-    a.slots_n += p.n_f[f];
-  }
-  a.slots_n = std::max(a.slots_n, 1);
+  a.n_ranges = p.dev.fam_order ? p.dev.n_ranges : 0;
+  for (int r = 0; r < a.n_ranges; r++) a.ranges[r] = p.dev.ranges[r];
   if (p.dev.two_sided) {
     a.snk_pos = p.dev.snk_lab2;
     a.snk_orig = p.dev.snk_order;
