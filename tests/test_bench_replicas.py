@@ -103,3 +103,23 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"] == "he4_n6_L48_4096x4096"
+
+
+def test_forward_launch_count():
+    """The bench's launch count: block factors (two launches when a flavour has n > 6),
+    one forward launch per group of families with the same flavour ranks (at most four),
+    and the reduction; built from the plan on the host."""
+    from paper_1411_3691_gb300 import mhc
+    from paper_1411_3691_gb300 import workloads as wl
+    he = bench.workload(0, scale=SCALE)
+    plan = mhc.Plan.from_workload(he)
+    assert bench.forward_launches(plan, he, plan.stats()) == 3
+    plan.close()
+    w = wl.make_workload("tworow", [12, 10], [60, 48], [9, 7, 5, 6, 8, 4], [8, 6, 7, 5, 30], seed=23,
+                         two_row_frac=0.5)
+    plan = mhc.Plan.from_workload(w)
+    ranks = plan.families()["rank"]
+    groups = {tuple(int(r) for r in row) for row in ranks}
+    assert len(groups) >= 2
+    assert bench.forward_launches(plan, w, plan.stats()) == 2 + min(len(groups), 4) + 1
+    plan.close()
