@@ -15,9 +15,11 @@
 // cof_A([A; h]) are taken from their definition (signed minors, fresh LU each).
 //
 // Scatter: each warp owns a private accumulator D[slot][label] (global memory, L1
-// resident) for its sinks; lane s owns row s (slot s < M: shared row m; slot M + c:
-// member c), so lanes never collide and every addition happens in a fixed order.  The
-// per-warp accumulators are summed in a fixed order by finalize kernels.
+// resident) for its sinks (slot s < M: shared row m; slot M + c: member c).  Rank-1
+// families deal the (slot, column) cells to the lanes, which add to distinct entries at
+// every step (scatter_rows); families of rank 2 and 3 give lane s row s (scatter_rowsk).
+// Either way every addition happens in a fixed order, and the per-warp accumulators are
+// summed in a fixed order by finalize kernels.
 #pragma once
 
 #include <type_traits>
@@ -925,7 +927,8 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
                                Ysm + (size_t)a.yoff[f] * T + tid, (pguard >> f) & 1, Binv, detB, myStage);
       __syncwarp();
 
-      // warp scatter: lane s owns accumulator row s (s < M: shared row; else member s - M)
+      // warp scatter: the block's (row, column) cells dealt to the lanes (rows s < M: shared
+      // rows; else member s - M)
       const int mynsh = qtwo ? n - a.q_rank[(int64_t)Q * a.F + f] : 0;
       const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
       const int nlive = rem < 32 ? (int)rem : 32;
