@@ -222,7 +222,9 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   // ---- per member: one dot product per flavour --------------------------------------
   double wj = valid ? a.w_snk[a.snk_orig ? a.snk_orig[j] : j] : 0.0;
   if (a.snk_orig && (__popc(a.snk_par[j]) & 1)) wj = -wj;
-  double2 acc = make_double2(0.0, 0.0);
+  // acc: sum over the members of w_i prod_f det (this lane's sink; times w_j once, at the
+  // end); accq: the refactored pairs, w_i w_j included (a queue lane holds other sinks' pairs)
+  double2 acc = make_double2(0.0, 0.0), accq = make_double2(0.0, 0.0);
   int qn = 0;
   unsigned long long n_parent = 0, n_child = 0;
   for (int c = 0; c < kW; c++) {
@@ -246,11 +248,11 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       }
     }
     const bool need = valid && fail != 0;
-    double w = a.w_src[a.mem_term[m]] * wj;
-    if (__popc(a.mem_par[m]) & 1) w = -w;
+    double wi = a.w_src[a.mem_term[m]];
+    if (__popc(a.mem_par[m]) & 1) wi = -wi;
     if (!fail) {
-      acc.x = fma(w, prod.x, acc.x);
-      acc.y = fma(w, prod.y, acc.y);
+      acc.x = fma(wi, prod.x, acc.x);
+      acc.y = fma(wi, prod.y, acc.y);
     }
     const unsigned ball = __ballot_sync(0xffffffffu, need);
     if (ball == 0xffffffffu) {
@@ -263,9 +265,9 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       e.fail = (int32_t)fail;
       e.pad = 0;
       e.prod = prod;
-      e.w = w;
+      e.w = wi * wj;
       e.pad2 = 0.0;
-      process_pairs<NCMAX>(a, W, true, e, j, acc);
+      process_pairs<NCMAX>(a, W, true, e, j, accq);
       n_parent += __popc(fail & pguard);
       n_child += __popc(fail & ~pguard);
     } else if (ball) {
@@ -277,7 +279,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
         e.fail = (int32_t)fail;
         e.pad = 0;
         e.prod = prod;
-        e.w = w;
+        e.w = wi * wj;
         e.pad2 = 0.0;
         queue[pos] = e;
         n_parent += __popc(fail & pguard);
@@ -286,7 +288,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       qn += __popc(ball);
       __syncwarp();
       if (qn >= 32) {
-        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, acc);
+        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, accq);
         __syncwarp();
         if (lane < qn - 32) queue[lane] = queue[32 + lane];
         __syncwarp();
@@ -294,7 +296,9 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       }
     }
   }
-  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, acc);
+  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, accq);
+  acc.x = fma(wj, acc.x, accq.x);
+  acc.y = fma(wj, acc.y, accq.y);
 
   // ---- fixed-order reduction: lanes, then warps --------------------------------------
   acc = dev::warp_sum(acc);

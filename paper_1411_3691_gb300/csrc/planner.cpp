@@ -645,10 +645,15 @@ mhc_status build_plan(Plan& p) {
   s.two_sided_blocks = two_blocks;
   int Fa = 0;
   for (int f = 0; f < F; f++) Fa += p.n_f[f] > 0;
-  const double combine = 6.0 * std::max(Fa - 1, 0) + 1.0 + 4.0;  // flavour product, w_i w_j, accumulate
-  fl += combine * (double)p.n_src * (double)p.n_snk;
+  // forward, per pair: the flavour product and w_i times it accumulated; per (family,
+  // sink): the sum times w_j, added to the refactored pairs' sum
+  const double combine = 6.0 * std::max(Fa - 1, 0) + 4.0;
+  fl += combine * (double)p.n_src * (double)p.n_snk + 4.0 * (double)p.n_fam * (double)p.n_snk;
   s.flops_per_call = fl;
-  s.backward_flops_per_call = bfl + (combine + 8.0) * (double)p.n_src * (double)p.n_snk;
+  // adjoint, per pair: the flavour product, w_i w_j, accumulate, and the combine of the
+  // weight gradients
+  const double bcombine = 6.0 * std::max(Fa - 1, 0) + 1.0 + 4.0 + 8.0;
+  s.backward_flops_per_call = bfl + bcombine * (double)p.n_src * (double)p.n_snk;
   double fresh = 0.0;
   for (int f = 0; f < F; f++) fresh += flops_fresh_lu(p.n_f[f]);
   s.fresh_lu_flops_per_pair = fresh + combine;
