@@ -36,7 +36,7 @@ UNIT = "pairs/s"
 NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per forward launch, from one ncu capture of
 # this workload (profiles/fwd_kernel_he4.md); None until captured for the current kernel.
-FWD_TRAFFIC_BYTES = 69.53e6  # 68.60 MB read + 0.93 MB write (fwd_kernel<8>, 2.071 ms launch)
+FWD_TRAFFIC_BYTES = 68.89e6  # 68.34 MB read + 0.55 MB write (fwd_kernel<8>, 2.040 ms launch)
 
 
 def parse():
