@@ -1,25 +1,34 @@
-"""Benchmark: the He-4-like correlator (2 flavours, n_f = 6, L = 48, 4096 x 4096 source x sink
-terms in families of 16) evaluated on the GPU through the C ABI.
+"""Benchmark: the large-nucleus correlator (2 flavours, n_f = 18, L = 96, 32768 x 32768 source x
+sink terms in families of 32, 10 % of the families with two changed rows, 1 % of the members
+forced near-singular) evaluated on the GPU through the C ABI, with the other workloads as
+sub-objects of the same line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mhc|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mhc|reference] [--workload NAME]
 
-One step = one mhc_correlator call (every step of the hot path: shared-row factorisation,
-cached solves, member dot products, refactors, fixed-order reduction) for one propagator
-set.  The plan (Sec. 3: graph + dominating set) is built once before timing, as the paper
-amortises it over gauge configurations.  Between timed steps L2 is flushed by writing a
-256 MiB buffer (outside the timed events).  Under torchrun every rank evaluates its own
-independent correlator (its own propagators: another gauge configuration), so the work per
-GPU is fixed ("weak" scaling) and no collective is on the data path; rank 0 prints one
-JSON line with the whole-job pairs/s over the slowest rank.
+One step = one mhc_correlator call (every step of the hot path: block factors, cached solves,
+member dot products, refactors of the guarded pairs, fixed-order reduction) for one
+propagator set.  The plan (Sec. 3: graph + dominating set) is built once before timing, as the
+paper amortises it over gauge configurations.  Between timed steps L2 is flushed by writing a
+256 MiB buffer (outside the timed events); the block factors of one call (9.7 GB) exceed L2 as
+well.  Under torchrun every rank evaluates its own independent correlator (its own
+propagators: another gauge configuration), so the work per GPU is fixed ("weak" scaling) and
+no collective is on the data path; rank 0 prints one JSON line with the whole-job pairs/s over
+the slowest rank.
 
---impl reference times the oracle (plain CPU FP64, fresh LU per pair) on the host cores on
-a bounded sample of the same workload, with the same metric.
+Sub-objects of the line (rank 0, N = 1 unless --headline-only):
+  one_sided  the same workload planned with opts.one_sided = 1 (Sec. 3 as printed: source
+             families only), time and fraction of the FP64 peak;
+  configs    the deuteron-like (512 x 512, n = 3) and He-4-like (4096 x 4096, n = 6) forward
+             calls, the 64-correlator batch (one CUDA graph vs 64 sequential calls) and the
+             adjoint on the He-4-like shapes (backward vs forward time).
+
+--impl reference times the oracle (plain CPU FP64, fresh LU per pair) on the host cores on a
+bounded sample of seeded pairs of the same workload, with the same metric.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -34,9 +43,13 @@ METRIC = "src×snk det pairs/sec (cplx FP64), % roofline; batched & adjoint vs p
 UNIT = "pairs/s"
 # FP64 peak from unit counts and clocks: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
 NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
-# dram__bytes_read.sum + dram__bytes_write.sum per forward launch, from one ncu capture of
-# this workload (profiles/fwd_kernel_he4.md); None until captured for the current kernel.
-FWD_TRAFFIC_BYTES = 68.89e6  # 68.34 MB read + 0.55 MB write (fwd_kernel<8>, 2.040 ms launch)
+# dram__bytes_read.sum + dram__bytes_write.sum of every kernel of one forward call, from one
+# ncu capture per workload (the large nucleus: a 1/8-per-side copy, 1/64 of the pairs and of the
+# block factors, scaled by 64).  None where no capture of the current kernels exists.
+TRAFFIC = {
+    "large": None,
+    "he4": None,
+}
 
 
 def parse():
@@ -45,13 +58,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mhc", choices=["mhc", "reference"])
-    ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "he4", "deuteron", "large_noforce", "large_small"],
+                    help="large (the benchmark line), he4, deuteron, or the n = 18 variants without "
+                         "forced members / at 1/8 scale per side (for profiler captures)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the selected workload only (no sub-objects, no CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-sequential comparison")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward comparison")
-    ap.add_argument("--workload", default="he4", choices=["he4", "large", "large_noforce", "large_small"],
-                    help="he4 (the benchmark line) or the n = 18 nucleus variants; the latter time "
-                         "the forward only (no adjoint, batch or CPU baseline)")
+    ap.add_argument("--scale", type=float, default=1.0, help=argparse.SUPPRESS)  # tests: shrink the workload
+    ap.add_argument("--cpu-pairs", type=int, default=100000,
+                    help="seeded (i, j) pairs the oracle evaluates for cpu_baseline / --impl reference")
     ap.add_argument("--fp64-peak", action="store_true",
                     help="only measure the FP64 (DFMA) peak: >= 1 s of independent chains on every SM, "
                          "SM clocks sampled meanwhile")
@@ -65,14 +81,14 @@ def dist_env():
     return rank, world, local
 
 
-def workload(rank: int, scale: float = 1.0, name: str = "he4"):
-    """The rank's own replica on its own propagators (seed).  he4: the He-4-like workload
-    of the benchmark line; large, large_noforce, large_small: the 32768 x 32768 n = 18
-    nucleus (10 % two-row families, 1 % forced near-singular members), the same without
-    the forced members, and a 1/8-scale copy of the first (for profiler captures)."""
+def workload(rank: int, name: str = "large", scale: float = 1.0):
+    """The rank's own replica on its own propagators (seed); scale < 1 shrinks the family
+    counts (tests)."""
     from paper_1411_3691_gb300 import workloads as wl
     if name == "he4":
         return wl.helium4(scale=scale, seed=1000 + 17 * rank)
+    if name == "deuteron":
+        return wl.deuteron(scale=scale, seed=17 * rank)
     if name == "large":
         return wl.large_nucleus(scale=scale, seed=3000 + 17 * rank)
     if name == "large_small":
@@ -119,26 +135,31 @@ def cores():
         return os.cpu_count() or 1
 
 
-def cpu_oracle_rate(w, seconds: float):
-    """Oracle pairs/s on the host cores over a bounded sample of source terms (all sinks)."""
+def oracle_pair_rate(w, n_pairs: int, seed: int = 31):
+    """The oracle (fresh partial-pivot LU per pair per flavour) on n_pairs seeded random
+    (i, j) pairs of the workload on all host cores, and the sampled pairs' share of C
+    (sum of w_i w_j prod_f det); returns (pairs/s, seconds, threads)."""
+    import numpy as np
+
     import oracle
     threads = cores()
-    n_snk = len(w.w_snk)
-    # calibrate on a small block, then size the sample for about `seconds`
+    rng = np.random.default_rng(seed)
+    ii = rng.integers(0, len(w.w_src), n_pairs)
+    jj = rng.integers(0, len(w.w_snk), n_pairs)
     t0 = time.perf_counter()
-    oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=threads,
-                      src_range=(0, min(len(w.w_src), 4 * threads)))
-    dt = max(time.perf_counter() - t0, 1e-3)
-    rate0 = min(len(w.w_src), 4 * threads) * n_snk / dt
-    n_src = int(min(len(w.w_src), max(threads, rate0 * seconds / n_snk)))
-    t0 = time.perf_counter()
-    C, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk,
-                                 threads=threads, src_range=(0, n_src))
+    d = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj, threads=threads)
+    _ = float(np.sum(w.w_src[ii] * w.w_snk[jj] * np.prod(d, axis=1)).real)
     dt = time.perf_counter() - t0
-    return {"value": n_src * n_snk / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n_src} of {len(w.w_src)} source terms x all {n_snk} sinks "
-                      f"({n_src * n_snk} pairs, fresh partial-pivot LU per pair per flavour), "
-                      f"{dt:.2f} s on {threads} threads"}
+    return n_pairs / dt, dt, threads
+
+
+def cpu_baseline(w, n_pairs: int):
+    rate, dt, threads = oracle_pair_rate(w, n_pairs)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_pairs} seeded random (i, j) pairs of the {len(w.w_src)} x {len(w.w_snk)} "
+                      f"workload (fresh partial-pivot LU per pair per flavour, w_i w_j prod det summed), "
+                      f"{dt:.2f} s on {threads} threads; rate extrapolated to all {w.pairs} pairs "
+                      f"({w.pairs / rate:.0f} s)"}
 
 
 class Clocks:
@@ -196,32 +217,64 @@ class Clocks:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
+def workload_config(w, st=None):
+    cfg = {"workload": w.name, "flavours": len(w.n_f), "n_f": w.n_f[0], "L": w.L_f[0],
+           "n_src": len(w.w_src), "n_snk": len(w.w_snk), "pairs_per_gpu": w.pairs}
+    if st is not None:
+        cfg.update({"families": st["families"], "sink_families": st["sink_families"],
+                    "two_row_family_flavours": st["rank2_family_flavours"]})
+    forced = w.meta.get("src", {}).get("forced") if w.meta else None
+    if forced:
+        cfg["forced_near_singular_member_flavours"] = len(forced)
+    return cfg
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = workload(0)
-    steps = []
-    per = max(args.cpu_sample_seconds / max(args.steps + args.warmup, 1), 0.5)
+    w = workload(0, args.workload, args.scale)
+    rates, secs = [], 0.0
+    threads = cores()
     for s in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(w, per)
+        r, dt, threads = oracle_pair_rate(w, args.cpu_pairs, seed=31 + s)
         if s >= args.warmup:
-            steps.append(r)
-    value = sum(r["value"] for r in steps) / len(steps)
-    cb = dict(steps[-1])
-    cb["value"] = value
+            rates.append(r)
+            secs += dt
+    value = sum(rates) / len(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "flavours": 2, "n_f": 6, "L": 48, "n_src": len(w.w_src),
-                       "n_snk": len(w.w_snk)},
-            "cpu_baseline": cb,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / len(rates) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"per step {args.cpu_pairs} seeded random (i, j) pairs of the "
+                                       f"{len(w.w_src)} x {len(w.w_snk)} workload (fresh partial-pivot LU "
+                                       f"per pair per flavour), rate extrapolated to all {w.pairs} pairs"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def time_forward(plan, S, out, flush, stream, steps: int, warmup: int = 2):
+    """Average CUDA-event time (ms) of one mhc_correlator call, L2 flushed between calls."""
+    import torch
+    for _ in range(warmup):
+        plan.correlator(S, out=out)
+    torch.cuda.synchronize()
+    plan.status()
+    tot = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.correlator(S, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    plan.status()
+    return tot / steps
+
+
 def run_gpu(args):
-    import numpy as np
     import torch
 
     from paper_1411_3691_gb300 import build as B
@@ -235,9 +288,8 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    w = workload(rank, name=args.workload)
-    if args.workload != "he4":  # the nucleus variants time the forward only
-        args.no_adjoint = args.no_batch = args.no_cpu_baseline = True
+    w = workload(rank, args.workload)
+    extras = not args.headline_only and world == 1 and rank == 0
     plan = mhc.Plan.from_workload(w)
     st = plan.stats()
     S = [torch.from_numpy(s).cuda() for s in w.S]
@@ -249,7 +301,7 @@ def run_gpu(args):
     # timed steps follow the warm-up directly
     peak_flops = mhc.mhc_fp64_peak(250000)
 
-    # warm-up (first call uploads the plan)
+    # warm-up (the first call uploads the plan)
     for _ in range(max(args.warmup, 3)):
         plan.correlator(S, out=out)
     torch.cuda.synchronize()
@@ -275,16 +327,16 @@ def run_gpu(args):
     plan.status()
     st = plan.stats()
     total_ms = max_over_ranks(total_ms, pg, "cuda")
-    pairs = len(w.w_src) * len(w.w_snk)
+    pairs = w.pairs
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, pairs, ms_per_step)
 
-    # roofline of the forward kernel (FP64 ALU bound): algorithmic flops per launch over the
-    # step's device time, against the FP64 peak measured above
-    # refactors are not counted (they run partly as shared factorisations of a group of
-    # pairs, below a fresh LU each): the FLOP figure is a lower bound of the work done
+    # roofline (FP64 ALU bound): algorithmic flops of one call -- the planned update scheme
+    # plus the refactor path as the device counted it -- over the whole step's device time
+    # (every launch of the call), against the FP64 peak measured above
     refactor_pairs = (st["refactor_parent"] + st["refactor_child"]) / max(args.steps, 1)
-    flops = st["flops_per_call"]
+    refactor_flops = st["refactor_flops"] / max(args.steps, 1)
+    flops = st["flops_per_call"] + refactor_flops
     achieved = flops / (ms_per_step * 1e-3) / 1e12
     peak = peak_flops / 1e12
 
@@ -299,65 +351,110 @@ def run_gpu(args):
         plan.correlator(dS, out=out)
         hout.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 10))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for k in range(args.steps):
+    for k in range(e2e_steps):
         for d, h in zip(dS, hS):
             d.copy_(h, non_blocking=True)
         plan.correlator(dS, out=out)
         hout.copy_(out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, pg, "cuda")
     h2d = sum(h.numel() * h.element_size() for h in hS)
+    plan.status()
+    C = [float(out[0].item()), float(out[1].item())]
 
-    adjoint = None if args.no_adjoint else time_adjoint(mhc, plan, S, flush, stream, ms_per_step, pairs)
-    batched = None if (args.no_batch or rank != 0) else time_batch(mhc, flush, stream)
+    launches = forward_launches(plan, w, st)
+    one_sided = configs = None
+    if extras:
+        one_sided = time_one_sided(mhc, w, S, out, flush, stream, ms_per_step, peak)
+    plan.close()
+    if extras:
+        configs = {
+            "deuteron": time_config(mhc, workload(0, "deuteron"), flush, stream, peak, steps=20),
+            "he4": time_config(mhc, workload(0, "he4"), flush, stream, peak, steps=20),
+            "batch": time_batch(mhc, flush, stream, peak),
+            "adjoint_he4": time_adjoint(mhc, workload(0, "he4"), flush, stream, peak),
+        }
 
-    if batched:
-        batched["frac_of_fp64_peak"] = batched["tflops"] / (peak_flops / 1e12)
-    if adjoint:
-        adjoint["frac_of_fp64_peak"] = adjoint["tflops"] / (peak_flops / 1e12)
-
-    line = None
     if rank == 0:
+        traffic = TRAFFIC.get(args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "flavours": len(w.n_f), "n_f": w.n_f[0], "L": w.L_f[0],
-                       "n_src": len(w.w_src),
-                       "n_snk": len(w.w_snk), "pairs_per_gpu": pairs, "families": st["families"],
-                       "parallelism": f"{world} independent correlators (one per GPU)",
-                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+            "config": dict(workload_config(w, st), **{
+                "parallelism": f"{world} independent correlators (one per GPU)",
+                "l2": "flushed between timed steps (256 MiB write outside the events); the call's "
+                      "block factors exceed L2"}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": FWD_TRAFFIC_BYTES if args.workload == "he4" else None,
+                         "traffic": traffic["bytes"] if traffic else None,
+                         "traffic_source": traffic["source"] if traffic else None,
                          "peak_source": "FP64 DFMA chains on all SMs, measured in this run "
                                         f"(nominal {NOMINAL_FP64_TFLOPS:.3f} from unit counts and clocks)",
-                         "flops_per_step": flops},
+                         "flops_per_step": flops,
+                         "flops_planned": st["flops_per_call"], "flops_refactor": refactor_flops,
+                         "time_base": "whole step (every launch of one call)"},
             "e2e": {"value": whole_job_rate(world, pairs, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": 16},
-            "gpu_launches": forward_launches(plan, w, st) * args.steps,
+                    "d2h_bytes_per_step": 16, "steps": e2e_steps},
+            "gpu_launches": launches * args.steps,
             "clocks": clocks,
             "refactors_per_step": refactor_pairs,
-            "adjoint": adjoint,
-            "batched": batched,
-            "C": [float(out[0].item()), float(out[1].item())],
+            "one_sided": one_sided,
+            "configs": configs,
+            "C": C,
         }
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_rate(w, args.cpu_sample_seconds)
+        if extras and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_pairs)
         print(json.dumps(line), flush=True)
-    plan.close()
     if pg:
         pg.barrier()
         pg.destroy_process_group()
 
 
-def time_adjoint(mhc, plan, S, flush, stream, fwd_ms, pairs, steps=5):
-    """Backward (dS_f, dw_src, dw_snk for L = Re C) of the same workload, CUDA events."""
+def time_one_sided(mhc, w, S, out, flush, stream, two_ms, peak):
+    """The same workload with opts.one_sided = 1: source families only, the shared rows
+    factorised per (family, sink, flavour) -- the execution order of Sec. 3 as printed."""
+    opts = mhc.default_opts()
+    opts.one_sided = 1
+    plan = mhc.Plan.from_workload(w, opts)
+    ms = time_forward(plan, S, out, flush, stream, steps=3, warmup=2)
+    st = plan.stats()
+    flops = st["flops_per_call"] + st["refactor_flops"] / 3
+    plan.close()
+    return {"ms_per_step": ms, "pairs_per_s": w.pairs / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12,
+            "frac_of_fp64_peak": flops / (ms * 1e-3) / 1e12 / peak, "flops_per_step": flops,
+            "two_sided_speedup": ms / two_ms}
+
+
+def time_config(mhc, w, flush, stream, peak, steps=20):
+    """Forward of another workload: CUDA-event time per call and fraction of the FP64 peak."""
     import torch
+    plan = mhc.Plan.from_workload(w)
+    S = [torch.from_numpy(s).cuda() for s in w.S]
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    ms = time_forward(plan, S, out, flush, stream, steps=steps)
+    st = plan.stats()
+    flops = st["flops_per_call"] + st["refactor_flops"] / steps
+    res = {"workload": w.name, "ms_per_step": ms, "pairs_per_s": w.pairs / (ms * 1e-3),
+           "tflops": flops / (ms * 1e-3) / 1e12, "frac_of_fp64_peak": flops / (ms * 1e-3) / 1e12 / peak,
+           "flops_per_step": flops, "gpu_launches_per_step": forward_launches(plan, w, st)}
+    plan.close()
+    return res
+
+
+def time_adjoint(mhc, w, flush, stream, peak, steps=10):
+    """Backward (dS_f, dw_src, dw_snk for L = Re C) of the He-4-like workload, CUDA events,
+    against its own forward call."""
+    import torch
+    plan = mhc.Plan.from_workload(w)
+    S = [torch.from_numpy(s).cuda() for s in w.S]
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    fwd_ms = time_forward(plan, S, out, flush, stream, steps=steps)
     g = torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda")
     dS = [torch.empty_like(s) for s in S]
     dws = torch.empty(plan.n_src, dtype=torch.float64, device="cuda")
@@ -376,16 +473,20 @@ def time_adjoint(mhc, plan, S, flush, stream, fwd_ms, pairs, steps=5):
         tot += e0.elapsed_time(e1)
     ms = tot / steps
     plan.status()
-    bflops = plan.stats()["backward_flops_per_call"]
-    return {"ms_per_step": ms, "ratio_vs_forward": ms / fwd_ms, "pairs_per_s": pairs / (ms * 1e-3),
-            "tflops": bflops / (ms * 1e-3) / 1e12, "flops_per_step": bflops,
-            "outputs": "dS_f (2 x 48 x 48 complex), dw_src [4096], dw_snk [4096]; L = Re C",
-            # block factors and B^-1 (two-sided plans), the adjoint kernel, one dS finalize per
-            # flavour, the two weight finalizes
-            "gpu_launches_per_step": (3 if plan.stats()["two_sided_blocks"] > 0 else 1) + len(S) + 2}
+    st = plan.stats()
+    bflops = st["backward_flops_per_call"]
+    res = {"workload": w.name, "ms_per_step": ms, "forward_ms_per_step": fwd_ms, "ratio_vs_forward": ms / fwd_ms,
+           "pairs_per_s": w.pairs / (ms * 1e-3), "tflops": bflops / (ms * 1e-3) / 1e12,
+           "frac_of_fp64_peak": bflops / (ms * 1e-3) / 1e12 / peak, "flops_per_step": bflops,
+           "outputs": "dS_f (2 x 48 x 48 complex), dw_src [4096], dw_snk [4096]; L = Re C",
+           # block factors and B^-1 (two-sided plans), the adjoint kernel, one dS finalize per
+           # flavour, the two weight finalizes
+           "gpu_launches_per_step": (3 if st["two_sided_blocks"] > 0 else 1) + len(S) + 2}
+    plan.close()
+    return res
 
 
-def time_batch(mhc, flush, stream, count=64, reps=3):
+def time_batch(mhc, flush, stream, peak, count=64, reps=10):
     """64 independent correlators of mixed n_f in one persistent launch under a CUDA graph,
     against 64 sequential mhc_correlator calls on the same plans and propagators."""
     import torch
@@ -394,7 +495,9 @@ def time_batch(mhc, flush, stream, count=64, reps=3):
     plans = [mhc.Plan.from_workload(w) for w in items]
     S = [[torch.from_numpy(s).cuda() for s in w.S] for w in items]
     pairs = sum(w.pairs for w in items)
+    t0 = time.perf_counter()
     batch = mhc.mhc_batch_create([p.handle for p in plans])
+    create_s = time.perf_counter() - t0
     T, n_items = mhc.mhc_batch_info(batch)
     outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in items]
     mhc.mhc_batch_correlator(batch, S, outs)
@@ -425,10 +528,10 @@ def time_batch(mhc, flush, stream, count=64, reps=3):
     return {"workload": f"{count} correlators: n_f ~ U{{3,6,9,12,18}} per flavour, L = 12 ceil(n/3) + 12, "
                         "terms per side log-U[256, 16384], family sizes U[1, 32] (seeds 2000 + b)",
             "pairs": pairs, "ms": batch_ms, "pairs_per_s": pairs / (batch_ms * 1e-3),
-            "tflops": flops / (batch_ms * 1e-3) / 1e12,
+            "tflops": flops / (batch_ms * 1e-3) / 1e12, "frac_of_fp64_peak": flops / (batch_ms * 1e-3) / 1e12 / peak,
             "sequential_ms": seq_ms, "sequential_pairs_per_s": pairs / (seq_ms * 1e-3),
-            "speedup_vs_sequential": seq_ms / batch_ms, "tile": T, "work_items": n_items,
-            "graph": True}
+            "speedup_vs_sequential": seq_ms / batch_ms, "reps": reps, "tile": T, "work_items": n_items,
+            "batch_create_s": create_s, "graph": True}
 
 
 def run_fp64_peak(args):

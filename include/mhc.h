@@ -109,7 +109,11 @@ typedef struct {
   int64_t two_sided_blocks;      /* (family, sink family, flavour) blocks sharing B's LU */
   double backward_flops_per_call;/* algorithmic FP64 flops of one mhc_correlator_backward */
   int64_t rank3_family_flavours; /* (family, flavour) blocks updated at rank 3        */
-  int64_t reserved[2];
+  double refactor_flops;         /* algorithmic FP64 flops of the refactor path in the calls
+                                    read by the last mhc_get_status (same counting rule as
+                                    flops_per_call; a group of pairs refactored together
+                                    counts its shared elimination once)                */
+  int64_t reserved[1];
 } mhc_stats;
 
 /* Thread-local message describing the last failure of this thread's last call. */
@@ -189,7 +193,11 @@ mhc_status mhc_plan_sinks(mhc_plan_t plan, int64_t* n_sink_families, int32_t* or
                           int32_t* labels, int32_t* parity, int32_t* family, int32_t* two_sided);
 
 /*
- * Forward correlator on the GPU.
+ * Forward correlator on the GPU: C = sum_i sum_j w_i w_j prod_f det G_f^{(ij)} for one gauge
+ * configuration (Sec. 1: the correlator as a double sum over wavefunction terms, G^{(ij)}
+ * gathered from the propagator, det G the product of the flavour blocks), each determinant
+ * by the update scheme of Sec. 2 (LU of the shared rows) and Sec. 2.1 (matrix determinant
+ * lemma with the solve G^{-1}e_r cached for every member that changes the same row).
  *   S_f        : host array of F device pointers, each complex128 L_f x L_f (may alias)
  *   w_src_dev  : device float64 [n_src] source weights, or NULL for the plan's
  *   w_snk_dev  : device float64 [n_snk] sink weights, or NULL for the plan's
@@ -250,7 +258,9 @@ mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
  *     mhc_correlator once with the plan first (that call allocates and uploads them).
  *     Otherwise MHC_EINVAL.
  *   - The first call on a device looks up the array's device address (a one-time set-up);
- *     make that first call before any stream capture.
+ *     make that first call before any stream capture.  The address is kept for the life of
+ *     the process: a cudaDeviceReset (which reloads the library's device code) is not
+ *     supported after that first call.
  *   - Every call shares the array, which keeps the last call's contents (each work item
  *     overwrites its own slot before it is read, so nothing needs clearing).  Calls that
  *     overlap on the GPU race on it: issue them on one stream or otherwise in order.
@@ -313,6 +323,17 @@ mhc_status mhc_batch_info(mhc_batch_t batch, int32_t* threads_per_block, int32_t
  * state the roofline denominator on the same GPU and clocks as a measurement.
  */
 mhc_status mhc_fp64_peak(int32_t iters, double* flops, mhc_stream_t stream);
+
+/*
+ * Diagnostic: the device complex reciprocal that every pivot of the factorisations uses,
+ * applied elementwise: out[i] = 1 / z[i] (z_dev, out_dev: device complex128 [n]).  It forms
+ * 1/z = conj(z) / |z|^2 with |z|^2 unscaled and 1/|z|^2 by Newton-Raphson refinement of the
+ * hardware approximation, so it is accurate for 2^-510 <= |z| <= 2^510 (outside, |z|^2
+ * leaves the normal range): there each component is within 5 u of the exact value's
+ * component (u = 2^-53; first-order bound 4 u).  Not a step of the paper's method; it lets
+ * a test state that accuracy.  Asynchronous on `stream`.
+ */
+mhc_status mhc_complex_reciprocal(int64_t n, const double* z_dev, double* out_dev, mhc_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -197,8 +197,9 @@ def correlator(S, n_f, labels_src, w_src, labels_snk, w_snk, threads: int = 1, s
     return complex(re, im), scale
 
 
-def pair_dets(S, n_f, labels_src, labels_snk, i_idx, j_idx):
-    """Per-pair per-flavour determinants, complex array [n_pairs, F]."""
+def pair_dets(S, n_f, labels_src, labels_snk, i_idx, j_idx, threads: int = 1):
+    """Per-pair per-flavour determinants, complex array [n_pairs, F].  ``threads`` > 1
+    splits the pair list into blocks evaluated in parallel (each pair is independent)."""
     lib = _load()
     n_src = np.asarray(labels_src).shape[0]
     n_snk = np.asarray(labels_snk).shape[0]
@@ -208,10 +209,21 @@ def pair_dets(S, n_f, labels_src, labels_snk, i_idx, j_idx):
     assert ii.shape == jj.shape
     assert (ii.size == 0) or (ii.min() >= 0 and ii.max() < n_src and jj.min() >= 0 and jj.max() < n_snk)
     out = np.zeros((ii.size, pr.F, 2))
-    rc = lib.oracle_pair_dets(*pr.head(), _p(pr.ls, _i32p), _p(pr.lk, _i32p), ii.size,
-                              _p(ii, _i64p), _p(jj, _i64p), _p(out, _f64p))
-    if rc != 0:
-        raise ValueError("oracle_pair_dets: bad argument")
+
+    def run(b):
+        a, e = b
+        rc = lib.oracle_pair_dets(*pr.head(), _p(pr.ls, _i32p), _p(pr.lk, _i32p), e - a,
+                                  _p(ii[a:], _i64p), _p(jj[a:], _i64p), _p(out[a:], _f64p))
+        if rc != 0:
+            raise ValueError("oracle_pair_dets: bad argument")
+
+    blocks = _blocks(ii.size, threads * 4 if threads > 1 else 1) or [(0, 0)]
+    if threads > 1 and len(blocks) > 1:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, blocks))
+    else:
+        for b in blocks:
+            run(b)
     return out[..., 0] + 1j * out[..., 1]
 
 

@@ -6,6 +6,7 @@
 
 #include "bwd_impl.cuh"
 #include "plan.h"
+#include "trace.h"
 
 namespace mhc {
 
@@ -131,6 +132,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
     return MHC_EINVAL;
   }
   Plan& p = *reinterpret_cast<Plan*>(plan);
+  TraceRange trace("mhc_correlator_backward");
   int max_rank = 1;  // families of rank k >= 2: k member rows per member, k^2 coefficients
   for (int64_t W = 0; W < p.n_fam; W++)
     for (int f = 0; f < p.F; f++) max_rank = std::max(max_rank, (int)p.fam_rank[W * p.F + f]);

@@ -14,6 +14,7 @@
 
 #include "kernels.cuh"
 #include "plan.h"
+#include "trace.h"
 
 struct mhc_batch_s;
 
@@ -315,6 +316,7 @@ void destroy(mhc_batch_s* b) {
 extern "C" {
 
 mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* plans) {
+  TraceRange trace("mhc_batch_create");
   if (!out || count <= 0 || !plans) {
     set_error("mhc_batch_create: bad argument");
     return MHC_EINVAL;
@@ -447,6 +449,7 @@ void mhc_batch_destroy(mhc_batch_t batch) { destroy(reinterpret_cast<mhc_batch_s
 
 mhc_status mhc_batch_correlator(mhc_batch_t batch, const double* const* const* S, double* const* outs,
                                 mhc_stream_t stream) {
+  TraceRange trace("mhc_batch_correlator");
   if (!batch || !S || !outs) {
     set_error("mhc_batch_correlator: NULL argument");
     return MHC_EINVAL;

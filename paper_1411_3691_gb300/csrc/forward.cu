@@ -1,6 +1,7 @@
 // forward.cu -- host launchers of the forward correlator and the deterministic reduction
 // of the per-work-item partial sums.
 #include "kernels.cuh"
+#include "trace.h"
 
 namespace mhc {
 
@@ -74,6 +75,7 @@ cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam,
                            size_t smem, double* out, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (a.snk_orig) {  // two-sided update: the LU factors of every (family, sink family) block first
+    TraceRange trace("block factors");
     if (ncmax <= 8)
       e = launch_kfac_nc8(a, n_fam, s);
     else if (ncmax <= 18)
@@ -82,7 +84,11 @@ cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam,
       e = launch_kfac_nc32(a, n_fam, s);
     if (e != cudaSuccess) return e;
   }
-  if ((e = launch_fwd_items(a, ncmax, tile, items, smem, s)) != cudaSuccess) return e;
+  {
+    TraceRange trace("forward kernel");
+    if ((e = launch_fwd_items(a, ncmax, tile, items, smem, s)) != cudaSuccess) return e;
+  }
+  TraceRange trace("reduce");
   return launch_reduce(a.partials, items, out, s);
 }
 

@@ -27,6 +27,27 @@ struct QEntry {
   double pad2;
 };
 
+// Algorithmic flops of the refactor path, counted with the planner's rule (real add/mul 1,
+// FMA 2, complex multiply 6, complex FMA 8, complex reciprocal 6, pivot measure 1):
+// a fresh partial-pivot LU determinant of one n x n block, ...
+__device__ __forceinline__ unsigned long long fresh_flops(int n) {
+  const long long m = n;
+  return (unsigned long long)(m * (m + 1) / 2 + 6 * (m - 1) + 3 * m * (m - 1) +
+                              8 * (m - 1) * m * (2 * m - 1) / 6 + 6 * (m - 1));
+}
+// ... the part of a grouped refactor (group_fresh) that the group shares: pivot search,
+// reciprocal, multipliers and updates of the first n - 1 columns, product of their pivots ...
+__device__ __forceinline__ unsigned long long group_shared_flops(int n) {
+  long long f = 0;
+  for (int k = 0; k + 1 < n; k++) f += (n - k) + 6 + 6 * (n - k - 1) + 8 * (n - k - 1) * (n - 2 - k);
+  return (unsigned long long)(f + 6 * (n > 2 ? n - 2 : 0));
+}
+// ... and the part of each pair of the group: its last column through the n - 1 steps,
+// the last pivot's measure and the product with it.
+__device__ __forceinline__ unsigned long long group_pair_flops(int n) {
+  return (unsigned long long)(4LL * n * (n - 1) + 1 + 6);
+}
+
 // Fresh determinants of a group of queued pairs that share member m and a two-sided sink
 // family Q with one changed column (flavour f; family of rank rho): their matrices agree in
 // the first n - 1 columns (the family's n - rho shared rows and the member's rho rows, in
@@ -128,7 +149,7 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
 // one per lane.  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& e, int64_t j,
-                              double2& acc) {
+                              double2& acc, unsigned long long& rflops) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int32_t* cols = dev::sink_cols(a, j);
@@ -148,13 +169,17 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
       const int lq = __shfl_sync(FULL, Q, leader);
       const unsigned grp = __ballot_sync(FULL, ((todo >> lane) & 1) && e.member == lm && Q == lq);
       const double2 d = group_fresh<NCMAX <= 18 ? NCMAX : 18>(a, W, f, rho, lm, lq, j, grp);
-      if ((grp >> lane) & 1) prod = dev::cmul(prod, d);
+      if ((grp >> lane) & 1) {
+        prod = dev::cmul(prod, d);
+        rflops += group_pair_flops(n) + (lane == leader ? group_shared_flops(n) : 0ull);
+      }
       todo &= ~grp;
     }
     if (need && !grouped) {
       dev::member_rows(a, W, e.member, f, rho, rows);
       const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, cols + a.off_f[f]);
       prod = dev::cmul(prod, d);
+      rflops += fresh_flops(n);
     }
   }
   if (have) {
@@ -166,12 +191,12 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
 // Refactor the first count queued pairs (one per lane).  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
-                              double2& acc) {
+                              double2& acc, unsigned long long& rflops) {
   const int lane = threadIdx.x & 31;
   const bool have = lane < count;
   QEntry e = {};
   if (have) e = q[lane];
-  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), acc);
+  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), acc, rflops);
 }
 
 // One work item (family W x sink tile) by the whole thread block; the block's sum goes
@@ -226,7 +251,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   // end); accq: the refactored pairs, w_i w_j included (a queue lane holds other sinks' pairs)
   double2 acc = make_double2(0.0, 0.0), accq = make_double2(0.0, 0.0);
   int qn = 0;
-  unsigned long long n_parent = 0, n_child = 0;
+  unsigned long long n_parent = 0, n_child = 0, rflops = 0;
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
     unsigned fail = pguard;
@@ -267,7 +292,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       e.prod = prod;
       e.w = wi * wj;
       e.pad2 = 0.0;
-      process_pairs<NCMAX>(a, W, true, e, j, accq);
+      process_pairs<NCMAX>(a, W, true, e, j, accq, rflops);
       n_parent += __popc(fail & pguard);
       n_child += __popc(fail & ~pguard);
     } else if (ball) {
@@ -288,7 +313,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       qn += __popc(ball);
       __syncwarp();
       if (qn >= 32) {
-        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, accq);
+        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, accq, rflops);
         __syncwarp();
         if (lane < qn - 32) queue[lane] = queue[32 + lane];
         __syncwarp();
@@ -296,7 +321,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       }
     }
   }
-  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, accq);
+  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, accq, rflops);
   acc.x = fma(wj, acc.x, accq.x);
   acc.y = fma(wj, acc.y, accq.y);
 
@@ -305,6 +330,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   for (int o = 16; o > 0; o >>= 1) {
     n_parent += __shfl_xor_sync(0xffffffffu, n_parent, o);
     n_child += __shfl_xor_sync(0xffffffffu, n_child, o);
+    rflops += __shfl_xor_sync(0xffffffffu, rflops, o);
   }
   __syncthreads();
   double2* red = smem;  // reuse: the factor cache is no longer needed
@@ -322,6 +348,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   if (lane == 0 && (n_parent | n_child)) {
     atomicAdd(&a.counters[1], n_parent);
     atomicAdd(&a.counters[2], n_child);
+    atomicAdd(&a.counters[3], rflops);
   }
 }
 

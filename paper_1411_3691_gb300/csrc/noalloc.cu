@@ -62,7 +62,6 @@ mhc_status scratch_for_current_device(double2** out) {
 }  // namespace
 
 int plan_ncmax(const Plan& p);
-int plan_tile(const Plan& p);
 mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
                          const double* w_snk, FwdArgs& a);
 
@@ -78,19 +77,20 @@ extern "C" mhc_status mhc_correlator_noalloc(mhc_plan_t plan, const double* cons
     return MHC_EINVAL;
   }
   Plan& p = *reinterpret_cast<Plan*>(plan);
-  const int tile = plan_tile(p);
-  const int64_t items = p.n_fam * ((p.n_snk + tile - 1) / tile);
-  if (items > kNoAllocMaxItems) {
-    set_error("mhc_correlator_noalloc: the plan has " + std::to_string(items) +
-              " work items (families x sink tiles); the fixed scratch holds at most " +
-              std::to_string(kNoAllocMaxItems) + ". Use mhc_correlator for this plan.");
-    return MHC_EINVAL;
-  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || p.dev.device != dev) {
     set_error("mhc_correlator_noalloc: the plan's tables are not on the current device yet; "
               "call mhc_correlator once with this plan on this device first (that call "
               "allocates and uploads them)");
+    return MHC_EINVAL;
+  }
+  // the launch shape the upload fixed (the same one mhc_correlator launches with)
+  const int tile = p.dev.tile;
+  const int64_t items = p.dev.n_items;
+  if (items > kNoAllocMaxItems) {
+    set_error("mhc_correlator_noalloc: the plan has " + std::to_string(items) +
+              " work items (families x sink tiles); the fixed scratch holds at most " +
+              std::to_string(kNoAllocMaxItems) + ". Use mhc_correlator for this plan.");
     return MHC_EINVAL;
   }
   double2* scratch = nullptr;

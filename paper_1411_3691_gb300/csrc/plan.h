@@ -59,7 +59,7 @@ struct DevicePlan {
   double* w_src = nullptr;       // [n_src] plan weights
   double* w_snk = nullptr;       // [n_snk]
   double* partials = nullptr;    // [items][2] per-work-item partial sums
-  unsigned long long* counters = nullptr;  // [4]: status bits, refactor parent, child, spare
+  unsigned long long* counters = nullptr;  // [4]: status bits, refactor parent, child, refactor flops
   int64_t n_items = 0;
   int32_t n_tiles = 0;           // sink tiles per family
   int32_t tile = 0;              // sinks per tile (threads per block)

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "plan.h"
+#include "trace.h"
 
 namespace mhc {
 
@@ -686,6 +687,7 @@ void mhc_plan_opts_default(mhc_plan_opts* o) {
 mhc_status mhc_plan(mhc_plan_t* out, int32_t F, const int32_t* n_f, const int32_t* L_f, int64_t n_src,
                     const int32_t* labels_src, const double* w_src, int64_t n_snk,
                     const int32_t* labels_snk, const double* w_snk, const mhc_plan_opts* opts) {
+  TraceRange trace("mhc_plan");
   if (!out) {
     set_error("mhc_plan: out is NULL");
     return MHC_EINVAL;

@@ -23,10 +23,33 @@ __global__ void __launch_bounds__(256) dfma_chains(double* out, int iters, doubl
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The complex reciprocal every pivot of the factorisations uses (dev::crcp), elementwise.
+__global__ void crcp_kernel(int64_t n, const double2* __restrict__ z, double2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = dev::crcp(z[i]);
+}
+
 }  // namespace
 }  // namespace mhc
 
 using namespace mhc;
+
+extern "C" mhc_status mhc_complex_reciprocal(int64_t n, const double* z_dev, double* out_dev,
+                                             mhc_stream_t stream) {
+  if (n < 0 || (n > 0 && (!z_dev || !out_dev))) {
+    set_error("mhc_complex_reciprocal: bad argument");
+    return MHC_EINVAL;
+  }
+  if (n == 0) return MHC_OK;
+  crcp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      n, reinterpret_cast<const double2*>(z_dev), reinterpret_cast<double2*>(out_dev));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("mhc_complex_reciprocal: ") + cudaGetErrorString(e));
+    return MHC_ECUDA;
+  }
+  return MHC_OK;
+}
 
 extern "C" mhc_status mhc_fp64_peak(int32_t iters, double* flops, mhc_stream_t stream) {
   if (iters <= 0 || !flops) {

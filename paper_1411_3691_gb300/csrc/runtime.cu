@@ -8,6 +8,7 @@
 
 #include "kernels.cuh"
 #include "plan.h"
+#include "trace.h"
 
 namespace mhc {
 
@@ -283,6 +284,7 @@ mhc_status mhc_correlator(mhc_plan_t plan, const double* const* S_f, const doubl
     return MHC_EINVAL;
   }
   Plan& p = *reinterpret_cast<Plan*>(plan);
+  TraceRange trace("mhc_correlator");
   mhc_status st = ensure_device(p);
   if (st != MHC_OK) return st;
   FwdArgs a;
@@ -351,6 +353,7 @@ mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream) {
   MHC_CUDA(cudaMemset(p.dev.counters, 0, sizeof(c)));
   p.stats.refactor_parent = (int64_t)c[1];
   p.stats.refactor_child = (int64_t)c[2];
+  p.stats.refactor_flops = (double)c[3];
   if (c[0] & kStatusTimeout) {
     set_error("a bounded device wait ran out");
     return MHC_ETIMEOUT;

@@ -31,7 +31,7 @@ EXPORTED = ["mhc_last_error", "mhc_plan_opts_default", "mhc_plan", "mhc_plan_des
             "mhc_correlator_cw",
             "mhc_correlator_backward",
             "mhc_pair_dets", "mhc_get_status", "mhc_batch_create", "mhc_batch_destroy",
-            "mhc_batch_correlator", "mhc_batch_info", "mhc_fp64_peak"]
+            "mhc_batch_correlator", "mhc_batch_info", "mhc_fp64_peak", "mhc_complex_reciprocal"]
 
 
 class MHCError(RuntimeError):
@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("refactor_parent", ctypes.c_int64),
                 ("refactor_child", ctypes.c_int64), ("sink_families", ctypes.c_int64),
                 ("two_sided_blocks", ctypes.c_int64), ("backward_flops_per_call", ctypes.c_double),
-                ("rank3_family_flavours", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
+                ("rank3_family_flavours", ctypes.c_int64), ("refactor_flops", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -98,6 +99,7 @@ def lib():
         L.mhc_batch_correlator.argtypes = [_vp, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(_vp), _vp]
         L.mhc_batch_info.argtypes = [_vp, _i32p, _i32p]
         L.mhc_fp64_peak.argtypes = [ctypes.c_int32, _f64p, _vp]
+        L.mhc_complex_reciprocal.argtypes = [ctypes.c_int64, _vp, _vp, _vp]
         for name in EXPORTED:
             if name not in ("mhc_last_error", "mhc_plan_opts_default", "mhc_plan_destroy",
                             "mhc_batch_destroy"):
@@ -303,6 +305,16 @@ def mhc_fp64_peak(iters: int = 200000, stream=None) -> float:
     f = ctypes.c_double()
     _check(lib().mhc_fp64_peak(iters, ctypes.byref(f), _stream(stream)))
     return f.value
+
+
+def mhc_complex_reciprocal(z, out=None, stream=None):
+    """1/z elementwise by the library's device reciprocal (z: complex128 CUDA tensor)."""
+    import torch
+    z = z.contiguous()
+    if out is None:
+        out = torch.empty_like(z)
+    _check(lib().mhc_complex_reciprocal(z.numel(), _ptr(z), _ptr(out), _stream(stream)))
+    return out
 
 
 # ------------------------------------------------------------------------------------------

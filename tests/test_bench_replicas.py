@@ -36,7 +36,7 @@ def _free_port():
 def _rank_main(rank, world, port, out_dir):
     import oracle
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
-    w = bench.workload(rank, scale=SCALE)
+    w = bench.workload(rank, "he4", scale=SCALE)
     t0 = time.perf_counter()
     C, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk)
     ms = (time.perf_counter() - t0) * 1e3
@@ -91,7 +91,7 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                                      "--cpu-sample-seconds", "0.5"])
+                                      "--cpu-pairs", "2000", "--scale", str(4 / 1024)])
     bench.main()
     lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -102,7 +102,8 @@ def test_reference_arm_json_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "pairs/s"
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
-    assert d["config"]["workload"] == "he4_n6_L48_4096x4096"
+    assert d["config"]["workload"] == "large_n18_L96_32768x32768"
+    assert d["config"]["n_f"] == 18 and d["config"]["L"] == 96
 
 
 def test_forward_launch_count():
@@ -111,7 +112,7 @@ def test_forward_launch_count():
     and the reduction; built from the plan on the host."""
     from paper_1411_3691_gb300 import mhc
     from paper_1411_3691_gb300 import workloads as wl
-    he = bench.workload(0, scale=SCALE)
+    he = bench.workload(0, "he4", scale=SCALE)
     plan = mhc.Plan.from_workload(he)
     assert bench.forward_launches(plan, he, plan.stats()) == 3
     plan.close()

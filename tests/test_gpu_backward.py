@@ -41,7 +41,7 @@ def gpu_backward(M, plan, S, g):
     return [d.cpu().numpy() for d in dS], dws.cpu().numpy(), dwk.cpu().numpy()
 
 
-def check_vs_oracle(M, w, opts=None):
+def check_vs_oracle(M, w, opts=None, threads=8):
     if opts is None:
         opts = M.default_opts()
         opts.rank2 = 1 if w.name in ("tc", "r2") else 0
@@ -49,7 +49,7 @@ def check_vs_oracle(M, w, opts=None):
     if w.name == "r2":
         assert plan.stats()["rank2_family_flavours"] > 0
     S = dev_S(w)
-    ref = oracle.correlator_grad(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    ref = oracle.correlator_grad(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=threads)
     worst = 0.0
     for g in ((1.0, 0.0), (0.0, 1.0), (0.6, -0.8)):
         gc = complex(*g)
@@ -168,10 +168,11 @@ def test_autograd_function(M):
     assert np.max(np.abs(wk.grad.cpu().numpy() - (np.conj(g) * ref["dw_snk"]).real)) <= 1e-10 * scale
 
 
-def test_full_helium4_fd_and_subplan(M):
+def test_full_helium4_fd_and_oracle(M):
     """4096 x 4096, n = 6: backward of Re C and Im C against central differences of the GPU
     forward on 200 random touched S entries (real and imaginary directions) and 200
-    weights, and against the oracle's Jacobi gradient on an 8-family sub-plan."""
+    weights, and the full problem's gradient (every dS_f entry, every weight, three loss
+    directions) against the oracle's Jacobi-formula gradient (cofactors from signed minors)."""
     w = wl.helium4()
     opts = M.default_opts()
     opts.rank2 = 0
@@ -220,10 +221,8 @@ def test_full_helium4_fd_and_subplan(M):
                 gr, gi = dwk_r[idx], dwk_i[idx]
             assert abs(fd.real - gr) <= 1e-9 * scale and abs(fd.imag - gi) <= 1e-9 * scale
     plan.close()
-    # Jacobi gradient of the oracle on a sub-plan: 8 families x all sinks
-    k = 8 * 16
-    sub = wl.Workload("sub", w.n_f, w.S, w.labels_src[:k], w.w_src[:k], w.labels_snk, w.w_snk)
-    check_vs_oracle(M, sub)
+    # Jacobi gradient of the oracle on the whole problem (same plan options)
+    check_vs_oracle(M, w, opts, threads=16)
 
 
 def test_two_row_guard_is_reported(M):

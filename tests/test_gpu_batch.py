@@ -6,6 +6,7 @@ import torch
 
 import oracle
 from paper_1411_3691_gb300 import workloads as wl
+from parity_util import check_pairs, family_mask, oracle_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -57,14 +58,26 @@ def test_batch_matches_oracle_and_plain(M):
 
 
 def test_full_batch_64_correlators(M):
-    """The 64-correlator batch of the benchmark, in its launch configuration (autotuned tile,
-    per-class persistent kernels, CUDA graph).  Correlators of at most 5e6 pairs and n_f <= 9:
-    C against the oracle.  Every correlator: C against one mhc_correlator call of the same
-    plan, within 1e-10 of a scale sum |w w prod det| that the oracle estimates from 2000
-    seeded pairs (exact for the small ones); and 200 seeded pairs through the per-pair probe
-    against the oracle's determinants."""
+    """The 64-correlator batch of the benchmark in its launch configuration (autotuned
+    shape, per-class persistent kernels, CUDA graph), every correlator against the oracle
+    at |dC| <= 1e-11 sum |w w prod det|:
+      * a correlator the oracle evaluates in seconds: its full C;
+      * any other: C with the source weights of all but 32 random families set to zero (the
+        planner ignores weight values, so the families, work items and launch are those of
+        the full plan) against the oracle's sum over those families x all sinks;
+    and for every correlator 10^4 seeded pairs through the per-pair probe at 1e-12 relative
+    (the conditioning bound where no FP64 method can reach that)."""
     items = wl.batch(64)
-    plans = [M.Plan.from_workload(w) for w in items]
+    budget = 5e6 * 2 * 9 ** 3          # pairs x sum_f n_f^3 of a full oracle evaluation
+    keeps, plans = [], []
+    for k, w in enumerate(items):
+        if w.pairs * sum(n ** 3 for n in w.n_f) <= budget:
+            keeps.append(None)
+            ws = w.w_src
+        else:
+            ws, keep = family_mask(w, 32, seed=640 + k)
+            keeps.append(keep)
+        plans.append(M.Plan(w.n_f, w.L_f, w.labels_src, ws, w.labels_snk, w.w_snk))
     S = [[torch.from_numpy(s).cuda() for s in w.S] for w in items]
     batch = M.mhc_batch_create([p.handle for p in plans])
     outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in items]
@@ -72,31 +85,21 @@ def test_full_batch_64_correlators(M):
     torch.cuda.synchronize()
     got = [complex(*o.cpu().numpy()) for o in outs]
     rng = np.random.default_rng(64)
-    n_oracle = 0
+    n_full = n_masked = 0
     for k, w in enumerate(items):
-        plain = complex(*plans[k].correlator(S[k]).cpu().numpy())
-        ns, nk = len(w.w_src), len(w.w_snk)
-        if w.pairs <= 5_000_000 and max(w.n_f) <= 9:
+        if keeps[k] is None:
             ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk,
                                            threads=16)
-            assert abs(got[k] - ref) <= 1e-11 * scale, (k, w.n_f, got[k], ref)
-            n_oracle += 1
+            n_full += 1
         else:
-            ii = rng.integers(0, ns, 2000)
-            jj = rng.integers(0, nk, 2000)
-            d = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj)
-            terms = np.abs(w.w_src[ii] * w.w_snk[jj] * np.prod(d, axis=1))
-            scale = float(np.mean(terms)) * w.pairs
-        assert abs(got[k] - plain) <= 1e-10 * scale, (k, w.n_f, got[k], plain)
-        ii = rng.integers(0, ns, 200)
-        jj = rng.integers(0, nk, 200)
-        gd = plans[k].pair_dets(S[k], torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()).cpu().numpy()
-        rd = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj)
-        for f, n in enumerate(w.n_f):
-            err = np.abs(gd[:, f] - rd[:, f])
-            assert np.all(err <= 1e-9 * np.abs(rd[:, f]) + 1e-300), (k, f, float(np.max(err / np.abs(rd[:, f]))))
-        M.mhc_get_status(plans[k].handle)
-    assert n_oracle >= 8
+            ref, scale = oracle_subset(w, keeps[k])
+            n_masked += 1
+        assert abs(got[k] - ref) <= 1e-11 * scale, (k, w.n_f, got[k], ref, abs(got[k] - ref) / scale)
+        ii = rng.integers(0, len(w.w_src), 10000)
+        jj = rng.integers(0, len(w.w_snk), 10000)
+        check_pairs(M, w, plans[k], S[k], ii, jj)
+        assert M.mhc_get_status_code(plans[k].handle) == M.MHC_OK
+    assert n_full >= 30 and n_masked >= 20
     M.mhc_batch_destroy(batch)
     for p in plans:
         p.close()

@@ -11,10 +11,9 @@ import torch
 
 import oracle
 from paper_1411_3691_gb300 import workloads as wl
+from parity_util import check_pairs, family_mask, oracle_subset
 
 pytestmark = pytest.mark.gpu
-
-U = 2.0 ** -53
 
 
 @pytest.fixture(scope="module")
@@ -106,32 +105,6 @@ def test_weights_override(M):
     assert abs(C - ref) <= 1e-11 * scale
 
 
-def check_pairs(M, w, plan, S, ii, jj):
-    it = torch.from_numpy(ii.astype(np.int64)).cuda()
-    jt = torch.from_numpy(jj.astype(np.int64)).cuda()
-    path = torch.zeros(len(ii), dtype=torch.int32, device="cuda")
-    got = plan.pair_dets(S, it, jt, path).cpu().numpy()
-    path = path.cpu().numpy()
-    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
-    ref = oracle.pair_dets(w.S, w.n_f, w.labels_src, w.labels_snk, ii, jj)
-    off = np.cumsum([0] + w.n_f)
-    n_ill = 0
-    for p in range(len(ii)):
-        for f, n in enumerate(w.n_f):
-            if n == 0:
-                continue
-            err = abs(got[p, f] - ref[p, f])
-            if err <= 1e-12 * abs(ref[p, f]):
-                continue
-            G = w.S[f][np.ix_(w.labels_src[ii[p], off[f]:off[f] + n], w.labels_snk[jj[p], off[f]:off[f] + n])]
-            kap = oracle.cond_inf(G)
-            hr, lr, hi, li = oracle.det_dd(G)
-            dd = complex(hr + lr, hi + li)
-            n_ill += 1
-            assert abs(got[p, f] - dd) <= 4 * n * U * kap * abs(dd) + 1e-300, (p, f, got[p, f], dd, kap)
-    return path, n_ill
-
-
 def test_pair_dets(M):
     w = CASES["large_rank2_forced"]
     plan = M.Plan.from_workload(w)
@@ -173,8 +146,11 @@ def test_full_helium4(M):
 
 
 def test_full_large_nucleus_sampled(M):
-    """32768 x 32768, n = 18: 10^5 seeded pairs through the probe against the oracle (the
-    launch configuration of the full plan), and C of a 4-family sub-plan x all sinks."""
+    """32768 x 32768, n = 18, in the plan and launch configuration the benchmark times:
+    10^5 seeded pairs through the probe against the oracle (1e-12 relative, or the
+    conditioning bound for the forced near-singular members, which must have taken the
+    refactor path), and C of the full plan with the source weights of all but 32 random
+    families set to zero against the oracle's sum over those families x all 32768 sinks."""
     w = wl.large_nucleus()
     plan = M.Plan.from_workload(w)
     S = dev_S(w)
@@ -182,13 +158,20 @@ def test_full_large_nucleus_sampled(M):
     ii = rng.integers(0, len(w.w_src), 100000)
     jj = rng.integers(0, len(w.w_snk), 100000)
     path, n_ill = check_pairs(M, w, plan, S, ii, jj)
+    forced = set(map(tuple, w.meta["src"]["forced"]))
+    for p in range(len(ii)):
+        for f in range(2):
+            if (int(ii[p]), f) in forced:
+                assert (path[p] >> f) & 1, (ii[p], jj[p], f)
+    ws, keep = family_mask(w, 32, seed=33)
+    assert len(keep) == 32 * 32
+    out = plan.correlator(S, torch.from_numpy(ws).cuda())
+    C = complex(*out.cpu().numpy())
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    assert plan.stats()["refactor_child"] > 0          # the forced members were refactored
+    ref, scale = oracle_subset(w, keep)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
     plan.close()
-    k = 4 * 32
-    sub = wl.Workload("sub", w.n_f, w.S, w.labels_src[:k], w.w_src[:k], w.labels_snk, w.w_snk)
-    C, plan, S = gpu_C(M, sub, S=S)
-    ref, scale = oracle.correlator(sub.S, sub.n_f, sub.labels_src, sub.w_src, sub.labels_snk, sub.w_snk,
-                                   threads=16)
-    assert abs(C - ref) <= 1e-11 * scale, (C, ref)
 
 
 def test_families_of_64(M):
