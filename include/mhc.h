@@ -234,9 +234,10 @@ mhc_status mhc_correlator_cw(mhc_plan_t plan, const double* const* S_f, const do
  * pointer to 2 doubles.  Any of dS_f (the whole array or single entries), dw_src_dev or
  * dw_snk_dev may be NULL to skip that output.  The dS_f buffers must not alias each
  * other.  Families of two or three changed rows are differentiated through the null
- * vectors of their shared rows; when those rows fail the pivot guard for some sink, that
- * block's dS_f contribution is left out and mhc_get_status returns MHC_EUNSUPPORTED (plan
- * with opts->rank2 = 0 for such inputs).  Not in the paper.
+ * vectors of their shared rows; where those rows fail the pivot guard for a sink, the null
+ * vectors are recomputed with complete pivoting, and where the shared rows are exactly
+ * rank-deficient (every member's determinant and member-row cofactor is then 0) the shared
+ * rows' cofactors come from signed minors.  Not in the paper.
  */
 mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
                                    const double* w_src_dev, const double* w_snk_dev,
@@ -286,16 +287,22 @@ mhc_status mhc_pair_dets(mhc_plan_t plan, const double* const* S_f, int64_t n_pa
 
 /*
  * Wait for the stream, read the plan's device status word and counters, clear them.
- * Returns MHC_OK, MHC_ENONFINITE, MHC_EINVAL (bad pair index), MHC_ETIMEOUT, or
- * MHC_EUNSUPPORTED (the adjoint left out a two-row family that failed the pivot guard).
+ * Returns MHC_OK, MHC_ENONFINITE, MHC_EINVAL (bad pair index) or MHC_ETIMEOUT.
  */
 mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream);
 
 /*
  * Batching: many independent correlators (each its own plan, flavour sizes and term
  * counts) in one persistent launch, captured once into a CUDA graph.
- * mhc_batch_create autotunes the launch shape on the current device (it runs the
- * kernels on scratch inputs and synchronises) and uploads the plans.
+ * mhc_batch_create splits the correlators by n class (largest n_f <= 8, <= 18, <= 32; one
+ * persistent kernel each) and chooses each class's sink tile (32, 64 or 128 threads per
+ * block, one thread per sink: 1, 2 or 4 warps) on the current device.  A class's tile is
+ * read from the tuning cache when the cache holds its key -- the GPU, this build of the
+ * library, the class and the (n_f, L_f) of its correlators -- and otherwise timed (the
+ * class's kernel alone on scratch propagators, every candidate tile) and written to the
+ * cache.  The cache is the file named by the environment variable MHC_TUNE_CACHE (empty:
+ * no cache), else $HOME/.cache/mhc/tune.jsonl, one JSON object per line.  The call
+ * synchronises and uploads the plans.
  *   plans : host array of `count` plans; they must outlive the batch.  A plan may appear
  *           more than once: one plan evaluated on several propagator sets (gauge
  *           configurations, time slices) in one launch, as the paper amortises the plan
@@ -314,8 +321,27 @@ void mhc_batch_destroy(mhc_batch_t batch);
 mhc_status mhc_batch_correlator(mhc_batch_t batch, const double* const* const* S,
                                 double* const* outs, mhc_stream_t stream);
 
-/* Autotuned launch shape of batch item b: threads per block and sink tile. */
+/* Launch shape of the batch: the sink tile (threads per block) of the n class with the most
+ * work items, and the total number of work items. */
 mhc_status mhc_batch_info(mhc_batch_t batch, int32_t* threads_per_block, int32_t* tiles_total);
+
+/*
+ * Chosen launch shape per n class (classes: largest n_f <= 8, <= 18, <= 32):
+ *   tiles      : host int32 [3], the sink tile (threads per block) of each class, 0 if unused
+ *   from_cache : host int32 [3] or NULL, 1 where the tile came from the tuning cache
+ *   tune_ms    : host float64 [3][3] or NULL, the class kernel's time (ms) at tiles 32, 64,
+ *                128 when it was timed (0: not timed, -1: did not fit in shared memory)
+ */
+mhc_status mhc_batch_shape(mhc_batch_t batch, int32_t* tiles, int32_t* from_cache, double* tune_ms);
+
+/*
+ * Tuning cache access (host only; see mhc_batch_create for the file and its keys).
+ * mhc_tune_cache_get writes the cached tile for `key` to *tile, or 0 when there is none.
+ * mhc_tune_cache_put appends `key` -> tile (32, 64 or 128); the key must hold no quote,
+ * backslash or newline.  MHC_EINVAL when the cache is disabled or not writable.
+ */
+mhc_status mhc_tune_cache_get(const char* key, int32_t* tile);
+mhc_status mhc_tune_cache_put(const char* key, int32_t tile);
 
 /*
  * FP64 peak probe: runs independent DFMA chains on every SM for about `iters` x 8 FMAs

@@ -1,5 +1,7 @@
 // batch.cu -- many independent correlators in one persistent launch, captured once into
-// a CUDA graph, with the sink tile (threads per block) chosen by measurement.
+// a CUDA graph, with the sink tile (threads per block: one thread per sink, so the tile is
+// also the number of warps per block times 32) chosen by measurement for each n class and
+// remembered in a small cache file.
 //
 // The work items of all correlators, (correlator, family, sink tile), are listed on the
 // host in decreasing order of their FLOP count (largest first), and a grid of one wave of
@@ -8,9 +10,20 @@
 // correlator's slots are summed in a fixed order afterwards: results do not depend on the
 // dynamic assignment.  There is no waiting between blocks, so no bounded wait is needed.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <set>
+#include <sstream>
 #include <string>
 #include <vector>
+
+#include <fcntl.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include "kernels.cuh"
 #include "plan.h"
@@ -77,9 +90,10 @@ __global__ void scratch_S(double2* S, int L, uint32_t seed) {
 constexpr int kClasses = 3;
 constexpr int kClassNc[kClasses] = {8, 18, 32};
 
-// One launch configuration of a batch (a sink tile T).
+// One launch configuration of a batch: a sink tile T[c] per n class.
 struct BatchShape {
-  int T = 0, ncmax = 8;
+  int T[kClasses] = {0, 0, 0};
+  int ncmax = 8;
   int64_t n_items = 0;
   std::vector<BatchItem> items;   // class by class, each in decreasing cost
   std::vector<int64_t> part_off;  // [count + 1]
@@ -117,7 +131,8 @@ struct mhc_batch_s {
   cudaStream_t side = nullptr;    // second branch: the class kernels run concurrently
   cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<const void*> key;  // S and out pointers the graph was captured with
-  std::vector<double> tune_ms;   // measured time per candidate tile (32, 64, 128)
+  double tune_ms[kClasses][3] = {};  // measured class time per candidate tile (32, 64, 128); 0: not run
+  int from_cache[kClasses] = {0, 0, 0};  // 1: the class's tile came from the tuning cache
 };
 
 namespace {
@@ -127,9 +142,9 @@ int class_of(const Plan& p) {
   return nc <= 8 ? 0 : (nc <= 18 ? 1 : 2);
 }
 
-BatchShape make_shape(const mhc_batch_s& b, int T) {
+BatchShape make_shape(const mhc_batch_s& b, const int (&Tc)[kClasses]) {
   BatchShape sh;
-  sh.T = T;
+  for (int c = 0; c < kClasses; c++) sh.T[c] = Tc[c];
   struct Cost {
     double c;
     BatchItem it;
@@ -139,8 +154,9 @@ BatchShape make_shape(const mhc_batch_s& b, int T) {
   int max_slots[kClasses] = {1, 1, 1};
   for (int k = 0; k < b.count; k++) {
     const Plan& p = *b.plans[k];
-    const int nt = (int)((p.n_snk + T - 1) / T);
     const int cl = class_of(p);
+    const int T = Tc[cl];
+    const int nt = (int)((p.n_snk + T - 1) / T);
     sh.n_tiles.push_back(nt);
     sh.ncmax = std::max(sh.ncmax, plan_ncmax(p));
     int yoff[MHC_FMAX], slots = 0;
@@ -168,10 +184,10 @@ BatchShape make_shape(const mhc_batch_s& b, int T) {
     for (auto& x : all[c]) sh.items.push_back(x.it);
     const int64_t n = (int64_t)all[c].size();
     if (n == 0) continue;
-    sh.cls_smem[c] = forward_smem_bytes(max_slots[c], T);
-    const int occ = c == 0 ? batch_occupancy_nc8(T, sh.cls_smem[c])
-                           : (c == 1 ? batch_occupancy_nc18(T, sh.cls_smem[c])
-                                     : batch_occupancy_nc32(T, sh.cls_smem[c]));
+    sh.cls_smem[c] = forward_smem_bytes(max_slots[c], Tc[c]);
+    const int occ = c == 0 ? batch_occupancy_nc8(Tc[c], sh.cls_smem[c])
+                           : (c == 1 ? batch_occupancy_nc18(Tc[c], sh.cls_smem[c])
+                                     : batch_occupancy_nc32(Tc[c], sh.cls_smem[c]));
     sh.cls_grid[c] = (int)std::min<int64_t>((int64_t)sms * occ, n);
   }
   sh.cls_off[kClasses] = (int64_t)sh.items.size();
@@ -179,10 +195,91 @@ BatchShape make_shape(const mhc_batch_s& b, int T) {
   return sh;
 }
 
-size_t max_smem(const BatchShape& sh) {
-  size_t m = 0;
-  for (int c = 0; c < kClasses; c++) m = std::max(m, sh.cls_smem[c]);
-  return m;
+// the tiles the tuner tries, and the shared memory limit a class's launch must fit in
+constexpr int kTiles[3] = {32, 64, 128};
+constexpr size_t kSmemLimit = 200 * 1024;
+
+// ---- tuning cache ---------------------------------------------------------------------
+// One JSON object per line: {"key": "...", "tile": T, "ms": [t32, t64, t128]}; the last
+// line with a key wins.  The file is MHC_TUNE_CACHE if that variable is set (empty: no
+// cache), else $HOME/.cache/mhc/tune.jsonl.  Lines are appended with one write() each.
+std::mutex g_cache_mutex;
+
+std::string cache_path() {
+  const char* e = std::getenv("MHC_TUNE_CACHE");
+  if (e) return std::string(e);
+  const char* h = std::getenv("HOME");
+  if (!h || !*h) return std::string();
+  const std::string dir = std::string(h) + "/.cache/mhc";
+  mkdir((std::string(h) + "/.cache").c_str(), 0755);
+  mkdir(dir.c_str(), 0755);
+  return dir + "/tune.jsonl";
+}
+
+bool cache_get(const std::string& key, int* tile) {
+  const std::string path = cache_path();
+  if (path.empty()) return false;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  std::ifstream in(path);
+  if (!in) return false;
+  const std::string want = "\"key\": \"" + key + "\"";
+  std::string line;
+  int found = 0;
+  while (std::getline(in, line)) {
+    if (line.find(want) == std::string::npos) continue;
+    const size_t t = line.find("\"tile\": ");
+    if (t == std::string::npos) continue;
+    const int v = std::atoi(line.c_str() + t + 8);
+    if (v == 32 || v == 64 || v == 128) found = v;
+  }
+  if (found) *tile = found;
+  return found != 0;
+}
+
+bool cache_put(const std::string& key, int tile, const double* ms) {
+  const std::string path = cache_path();
+  if (path.empty()) return false;
+  std::ostringstream o;
+  o << "{\"key\": \"" << key << "\", \"tile\": " << tile << ", \"ms\": [";
+  for (int i = 0; i < 3; i++) o << (i ? ", " : "") << (ms ? ms[i] : 0.0);
+  o << "]}\n";
+  const std::string line = o.str();
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  const int fd = open(path.c_str(), O_WRONLY | O_CREAT | O_APPEND, 0644);
+  if (fd < 0) return false;
+  const bool ok = write(fd, line.data(), line.size()) == (ssize_t)line.size();
+  close(fd);
+  return ok;
+}
+
+// The cache key of class c of a batch: the GPU, this build of the library, the class and
+// the (n_f, L_f) signatures of its correlators.
+std::string class_key(const mhc_batch_s& b, int c) {
+  std::set<std::string> sig;
+  for (const Plan* p : b.plans) {
+    if (class_of(*p) != c) continue;
+    std::ostringstream o;
+    for (int f = 0; f < p->F; f++) o << (f ? "," : "") << p->n_f[f] << "/" << p->L_f[f];
+    sig.insert(o.str());
+  }
+  if (sig.empty()) return std::string();
+  cudaDeviceProp prop;
+  std::string gpu = "unknown";
+  if (cudaGetDeviceProperties(&prop, b.device) == cudaSuccess) {
+    gpu = prop.name;
+    gpu += " sm" + std::to_string(prop.multiProcessorCount);
+  }
+  std::ostringstream o;
+  o << "gpu=" << gpu << ";build=" << __DATE__ << " " << __TIME__ << ";nc=" << kClassNc[c] << ";shapes=";
+  bool first = true;
+  for (const auto& x : sig) {
+    o << (first ? "" : " ") << x;
+    first = false;
+  }
+  std::string k = o.str();
+  for (char& ch : k)
+    if (ch == '"' || ch == '\\' || ch == '\n') ch = '_';
+  return k;
 }
 
 mhc_status fill_descs(mhc_batch_s& b, const BatchShape& sh, const double* const* const* S,
@@ -237,14 +334,21 @@ cudaError_t launch_class(const mhc_batch_s& b, const BatchShape& sh, int c, cuda
   const BatchItem* items = b.d_items + sh.cls_off[c];
   const int64_t n = sh.cls_off[c + 1] - sh.cls_off[c];
   unsigned long long* head = b.d_head + c;
+  const int T = sh.T[c];
   if (c == 0)
-    return launch_batch_nc8(sh.cls_grid[c], sh.T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
+    return launch_batch_nc8(sh.cls_grid[c], T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
                             b.d_partials);
   if (c == 1)
-    return launch_batch_nc18(sh.cls_grid[c], sh.T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
+    return launch_batch_nc18(sh.cls_grid[c], T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
                              b.d_partials);
-  return launch_batch_nc32(sh.cls_grid[c], sh.T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
+  return launch_batch_nc32(sh.cls_grid[c], T, sh.cls_smem[c], s, b.d_desc, items, n, head, b.d_part_off,
                            b.d_partials);
+}
+
+cudaError_t launch_kfac(const mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
+  if (sh.ncmax <= 8) return launch_kfac_batch_nc8(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
+  if (sh.ncmax <= 18) return launch_kfac_batch_nc18(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
+  return launch_kfac_batch_nc32(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
 }
 
 cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
@@ -252,13 +356,7 @@ cudaError_t enqueue(mhc_batch_s& b, const BatchShape& sh, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // two-sided update: the factors of every (family, sink family) block of every
   // correlator, in one launch (two when some flavour has n > 6)
-  if (sh.ncmax <= 8)
-    e = launch_kfac_batch_nc8(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
-  else if (sh.ncmax <= 18)
-    e = launch_kfac_batch_nc18(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
-  else
-    e = launch_kfac_batch_nc32(b.d_desc, b.d_kpref, b.d_nfam, b.count, b.k_total, b.k_big, s);
-  if (e != cudaSuccess) return e;
+  if ((e = launch_kfac(b, sh, s)) != cudaSuccess) return e;
   // the class with the most work on s, the others on the side branch: a class's blocks
   // take the SMs that the other class's queue releases as it drains
   int main_cls = -1;
@@ -366,77 +464,108 @@ mhc_status mhc_batch_create(mhc_batch_t* out, int32_t count, const mhc_plan_t* p
     set_error("mhc_batch_create: CUDA allocation failed");
     return MHC_ENOMEM;
   }
-  // ---- autotune the sink tile on scratch propagators -------------------------------
-  std::vector<std::vector<double2*>> scratch(count);
-  std::vector<std::vector<const double*>> sp(count);
-  std::vector<const double* const*> S(count);
-  double* scratch_out = nullptr;
-  cudaMalloc(&scratch_out, sizeof(double) * 2 * count);
-  std::vector<double*> outs(count);
-  for (int k = 0; k < count; k++) {
-    const Plan& p = *b->plans[k];
-    for (int f = 0; f < p.F; f++) {
-      double2* s = nullptr;
-      const int L = p.L_f[f];
-      if (cudaMalloc(&s, sizeof(double2) * L * L) != cudaSuccess) {
-        destroy(b);
-        set_error("mhc_batch_create: scratch allocation failed");
-        return MHC_ENOMEM;
-      }
-      scratch_S<<<(L * L + 255) / 256, 256, 0, b->cap>>>(s, L, 977u * k + f);
-      scratch[k].push_back(s);
-      sp[k].push_back(reinterpret_cast<const double*>(s));
+  // ---- the sink tile of each n class: from the tuning cache, else timed on scratch
+  // propagators (each class's persistent kernel alone, after the block factors) --------
+  int Tc[kClasses] = {32, 32, 32};
+  bool present[kClasses] = {false, false, false}, tune[kClasses] = {false, false, false};
+  std::string keys[kClasses];
+  for (const Plan* p : b->plans) present[class_of(*p)] = true;
+  bool any_tune = false;
+  for (int c = 0; c < kClasses; c++) {
+    if (!present[c]) continue;
+    keys[c] = class_key(*b, c);
+    if (cache_get(keys[c], &Tc[c])) {
+      b->from_cache[c] = 1;
+    } else {
+      tune[c] = true;
+      any_tune = true;
     }
-    S[k] = sp[k].data();
-    outs[k] = scratch_out + 2 * k;
   }
-  cudaMemcpy(b->d_outs, outs.data(), sizeof(double*) * count, cudaMemcpyHostToDevice);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  double best = 1e300;
-  const int cands[3] = {32, 64, 128};
   mhc_status st = MHC_OK;
-  for (int T : cands) {
-    BatchShape sh = make_shape(*b, T);
-    if (max_smem(sh) > 200 * 1024) {
-      b->tune_ms.push_back(-1.0);
-      continue;
+  if (any_tune) {
+    std::vector<std::vector<double2*>> scratch(count);
+    std::vector<std::vector<const double*>> sp(count);
+    std::vector<const double* const*> S(count);
+    double* scratch_out = nullptr;
+    std::vector<double*> outs(count);
+    if (cudaMalloc(&scratch_out, sizeof(double) * 2 * count) != cudaSuccess) st = MHC_ENOMEM;
+    for (int k = 0; k < count && st == MHC_OK; k++) {
+      const Plan& p = *b->plans[k];
+      for (int f = 0; f < p.F; f++) {
+        double2* sc = nullptr;
+        const int L = p.L_f[f];
+        if (cudaMalloc(&sc, sizeof(double2) * L * L) != cudaSuccess) {
+          st = MHC_ENOMEM;
+          break;
+        }
+        scratch_S<<<(L * L + 255) / 256, 256, 0, b->cap>>>(sc, L, 977u * k + f);
+        scratch[k].push_back(sc);
+        sp[k].push_back(reinterpret_cast<const double*>(sc));
+      }
+      S[k] = sp[k].data();
+      outs[k] = scratch_out + 2 * k;
     }
-    std::vector<FwdArgs> desc;
-    if ((st = fill_descs(*b, sh, S.data(), desc)) != MHC_OK) break;
-    cudaMemcpy(b->d_desc, desc.data(), sizeof(FwdArgs) * count, cudaMemcpyHostToDevice);
-    b->h_desc = desc;
-    if ((st = upload_shape(*b, sh)) != MHC_OK) break;
-    float ms = 0.f;
-    for (int rep = 0; rep < 2; rep++) {
-      cudaEventRecord(e0, b->cap);
-      cudaError_t e = enqueue(*b, sh, b->cap);
-      cudaEventRecord(e1, b->cap);
-      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+    if (st == MHC_ENOMEM) set_error("mhc_batch_create: scratch allocation failed");
+    if (st == MHC_OK)
+      cudaMemcpy(b->d_outs, outs.data(), sizeof(double*) * count, cudaMemcpyHostToDevice);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int ti = 0; ti < 3 && st == MHC_OK; ti++) {
+      int Tt[kClasses];
+      for (int c = 0; c < kClasses; c++) Tt[c] = tune[c] ? kTiles[ti] : Tc[c];
+      BatchShape sh = make_shape(*b, Tt);
+      std::vector<FwdArgs> desc;
+      if ((st = fill_descs(*b, sh, S.data(), desc)) != MHC_OK) break;
+      cudaMemcpy(b->d_desc, desc.data(), sizeof(FwdArgs) * count, cudaMemcpyHostToDevice);
+      b->h_desc = desc;
+      if ((st = upload_shape(*b, sh)) != MHC_OK) break;
+      cudaError_t e = launch_kfac(*b, sh, b->cap);
+      for (int c = 0; c < kClasses && e == cudaSuccess; c++) {
+        if (!tune[c]) continue;
+        if (sh.cls_smem[c] > kSmemLimit) {
+          b->tune_ms[c][ti] = -1.0;
+          continue;
+        }
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+          e = cudaMemsetAsync(b->d_head + c, 0, sizeof(unsigned long long), b->cap);
+          if (e == cudaSuccess) e = cudaEventRecord(e0, b->cap);
+          if (e == cudaSuccess) e = launch_class(*b, sh, c, b->cap);
+          if (e == cudaSuccess) e = cudaEventRecord(e1, b->cap);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        b->tune_ms[c][ti] = ms;
+      }
+      if (e != cudaSuccess) {
         set_error(std::string("mhc_batch_create: tuning launch failed: ") + cudaGetErrorString(e));
         st = MHC_ECUDA;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (auto& v : scratch)
+      for (auto* x : v) cudaFree(x);
+    if (scratch_out) cudaFree(scratch_out);
+    for (int c = 0; c < kClasses && st == MHC_OK; c++) {
+      if (!tune[c]) continue;
+      int best = -1;
+      for (int ti = 0; ti < 3; ti++)
+        if (b->tune_ms[c][ti] > 0.0 && (best < 0 || b->tune_ms[c][ti] < b->tune_ms[c][best])) best = ti;
+      if (best < 0) {
+        set_error("mhc_batch_create: no launch shape fits in shared memory");
+        st = MHC_EUNSUPPORTED;
         break;
       }
-      cudaEventElapsedTime(&ms, e0, e1);
-    }
-    if (st != MHC_OK) break;
-    b->tune_ms.push_back(ms);
-    if (ms < best) {
-      best = ms;
-      b->shape = std::move(sh);
+      Tc[c] = kTiles[best];
+      cache_put(keys[c], Tc[c], b->tune_ms[c]);
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  for (auto& v : scratch)
-    for (auto* s : v) cudaFree(s);
-  cudaFree(scratch_out);
-  if (st == MHC_OK && b->shape.T == 0) {
-    set_error("mhc_batch_create: no launch shape fits in shared memory");
-    st = MHC_EUNSUPPORTED;
+  if (st == MHC_OK) {
+    b->shape = make_shape(*b, Tc);
+    st = upload_shape(*b, b->shape);
   }
-  if (st == MHC_OK) st = upload_shape(*b, b->shape);
   if (st != MHC_OK) {
     destroy(b);
     return st;
@@ -509,8 +638,52 @@ mhc_status mhc_batch_info(mhc_batch_t batch, int32_t* threads_per_block, int32_t
     return MHC_EINVAL;
   }
   const mhc_batch_s& b = *reinterpret_cast<const mhc_batch_s*>(batch);
-  if (threads_per_block) *threads_per_block = b.shape.T;
+  int main_cls = 0;  // the class with the most work items
+  for (int c = 1; c < kClasses; c++)
+    if (b.shape.cls_off[c + 1] - b.shape.cls_off[c] > b.shape.cls_off[main_cls + 1] - b.shape.cls_off[main_cls])
+      main_cls = c;
+  if (threads_per_block) *threads_per_block = b.shape.T[main_cls];
   if (tiles_total) *tiles_total = (int32_t)b.shape.n_items;
+  return MHC_OK;
+}
+
+mhc_status mhc_batch_shape(mhc_batch_t batch, int32_t* tiles, int32_t* from_cache, double* tune_ms) {
+  if (!batch || !tiles) {
+    set_error("mhc_batch_shape: NULL batch or tiles");
+    return MHC_EINVAL;
+  }
+  const mhc_batch_s& b = *reinterpret_cast<const mhc_batch_s*>(batch);
+  for (int c = 0; c < kClasses; c++) {
+    const bool used = b.shape.cls_off[c + 1] > b.shape.cls_off[c];
+    tiles[c] = used ? b.shape.T[c] : 0;
+    if (from_cache) from_cache[c] = used ? b.from_cache[c] : 0;
+    if (tune_ms)
+      for (int t = 0; t < 3; t++) tune_ms[3 * c + t] = b.tune_ms[c][t];
+  }
+  return MHC_OK;
+}
+
+mhc_status mhc_tune_cache_get(const char* key, int32_t* tile) {
+  if (!key || !tile) {
+    set_error("mhc_tune_cache_get: NULL argument");
+    return MHC_EINVAL;
+  }
+  int t = 0;
+  *tile = cache_get(key, &t) ? t : 0;
+  return MHC_OK;
+}
+
+mhc_status mhc_tune_cache_put(const char* key, int32_t tile) {
+  if (!key || !*key || !(tile == 32 || tile == 64 || tile == 128) || std::strchr(key, '"') ||
+      std::strchr(key, '\\') || std::strchr(key, '\n')) {
+    set_error("mhc_tune_cache_put: key must be non-empty without quotes, backslashes or newlines; "
+              "tile 32, 64 or 128");
+    return MHC_EINVAL;
+  }
+  if (!cache_put(key, tile, nullptr)) {
+    set_error("mhc_tune_cache_put: the cache file is disabled (MHC_TUNE_CACHE empty) or not writable");
+    return MHC_EINVAL;
+  }
   return MHC_OK;
 }
 

@@ -385,14 +385,200 @@ __device__ __forceinline__ void adjugate(const cd (&D)[RK][RK], cd (&adj)[RK][RK
   }
 }
 
+// The rank-k block of one sink when the shared rows' factorisation fails the pivot guard
+// (the first n - k columns of A nearly singular, or A itself rank-deficient, e.g. a repeated
+// shared label).  The member rows' cofactors always lie in the null space of A: every shared
+// row is orthogonal (bilinearly) to them.
+//   * A of full rank: an LU of A with complete pivoting, P A Pi = L [U1 | U2], picks the n - k
+//     pivot columns; the null vectors z'_v (unit entry at the v-th free column, -U1^{-1}U2 e_v
+//     at the pivot columns) and sd' = sign(P) sign(Pi) det(U1) satisfy det [A; B] =
+//     sd' det(B Z'), and X0 = Pi [A1'^{-1}; 0] is a right inverse of A, so the formulas of
+//     cof_passk hold with (Z', sd', X0) -- the derivation only uses A X0 = I and A Z' = 0.
+//     Z' and sd' replace the sink's cached solves, which the scatter reads.
+//   * A rank-deficient (an exactly zero pivot): every member's [A; B] is singular and every
+//     member-row cofactor is a minor of rank below its size, so exactly 0; the shared rows'
+//     block sum_c gamma_c cof(G_c)[A] is taken from signed minors (fresh LU each).
 template <int NC, int RK>
-__device__ __noinline__ void cof_passk(const FwdArgs& a, int f, int n, int mem0, int kW, int tid,
+__device__ __noinline__ void cof_passk_guarded(const FwdArgs& a, int f, int n, int mem0, int kW, int tid,
+                                               int T, int kmax, const int32_t* __restrict__ col,
+                                               const int32_t* __restrict__ arow, const cd* Dets, cd* Y,
+                                               cd* Mst, cd* R) {
+  constexpr int MC = NC - RK > 0 ? NC - RK : 1;
+  const int M = n - RK;
+  const cd* S = a.S[f];
+  const int L = a.L_f[f];
+  cd A[NC][NC];  // the shared rows (complete-pivoting LU), or [A; B_c] for the minors
+  int rp[MC], cp[NC];
+  for (int i = 0; i < M; i++) {
+    rp[i] = i;
+    const cd* row = S + (size_t)arow[i] * L;
+    for (int q = 0; q < n; q++) A[i][q] = dev::ldS(row + col[q]);
+  }
+  for (int q = 0; q < n; q++) cp[q] = q;
+  int parity = 0;
+  bool degenerate = false;
+  cd det = make_double2(1.0, 0.0);
+  cd rc[MC];
+  for (int t = 0; t < M; t++) {
+    // complete pivoting: the largest |re| + |im| of the remaining block, first in row-major order
+    int pi = t, pq = t;
+    double best = -1.0;
+    for (int i = t; i < M; i++)
+      for (int q = t; q < n; q++) {
+        const double v = dev::abs1(A[i][q]);
+        if (best < 0.0 || dev::gt_nonneg(v, best)) {
+          best = v;
+          pi = i;
+          pq = q;
+        }
+      }
+    if (__double_as_longlong(best) == 0) {
+      degenerate = true;
+      break;
+    }
+    if (pi != t) {
+      for (int q = 0; q < n; q++) {
+        const cd x = A[t][q];
+        A[t][q] = A[pi][q];
+        A[pi][q] = x;
+      }
+      const int x = rp[t];
+      rp[t] = rp[pi];
+      rp[pi] = x;
+      parity ^= 1;
+    }
+    if (pq != t) {
+      for (int i = 0; i < M; i++) {
+        const cd x = A[i][t];
+        A[i][t] = A[i][pq];
+        A[i][pq] = x;
+      }
+      const int x = cp[t];
+      cp[t] = cp[pq];
+      cp[pq] = x;
+      parity ^= 1;
+    }
+    det = t == 0 ? A[t][t] : dev::cmul(det, A[t][t]);
+    rc[t] = dev::crcp(A[t][t]);
+    for (int i = t + 1; i < M; i++) {
+      const cd l = dev::cmul(A[i][t], rc[t]);
+      A[i][t] = l;
+      for (int q = t + 1; q < n; q++) A[i][q] = dev::cfms(l, A[t][q], A[i][q]);
+    }
+  }
+  if (degenerate) {
+    for (int v = 0; v < RK; v++)
+      for (int q = 0; q < n; q++) Y[(size_t)(v * n + q) * T] = make_double2(0.0, 0.0);
+    Y[(size_t)RK * n * T] = make_double2(0.0, 0.0);
+    for (int c = 0; c < kW; c++)
+      for (int t = 0; t < RK * RK; t++) R[((size_t)c * RK * RK + t) * T + tid] = make_double2(0.0, 0.0);
+    for (int e = 0; e < M * n; e++) Mst[e] = make_double2(0.0, 0.0);
+    for (int i = 0; i < M; i++)
+      for (int q = 0; q < n; q++) A[i][q] = dev::ldS(S + (size_t)arow[i] * L + col[q]);
+    for (int c = 0; c < kW; c++) {
+      const int m = mem0 + c;
+      const cd g = Dets[dix(c, f, kmax, T, tid)];  // gamma_c of this flavour
+      for (int u = 0; u < RK; u++) {
+        const cd* br = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + u] * L;
+        for (int q = 0; q < n; q++) A[M + u][q] = dev::ldS(br + col[q]);
+      }
+      for (int i = 0; i < M; i++)
+        for (int q = 0; q < n; q++) Mst[i * n + q] = dev::cfma(g, signed_minor<NC>(A, n, i, q), Mst[i * n + q]);
+    }
+    return;
+  }
+  const cd sd = parity ? dev::cneg(det) : det;
+  // null vectors in the original column order, written over the sink's cached solves
+  for (int v = 0; v < RK; v++) {
+    cd w[MC];
+    for (int p = M - 1; p >= 0; p--) {
+      cd x = A[p][M + v];
+      for (int q = p + 1; q < M; q++) x = dev::cfma(A[p][q], w[q], x);
+      w[p] = dev::cmul(x, dev::cneg(rc[p]));
+    }
+    for (int q = 0; q < M; q++) Y[(size_t)(v * n + cp[q]) * T] = w[q];
+    for (int u = 0; u < RK; u++) Y[(size_t)(v * n + cp[M + u]) * T] = make_double2(u == v ? 1.0 : 0.0, 0.0);
+  }
+  Y[(size_t)RK * n * T] = sd;
+  // members: D = B Z', adj(D), s, E, the member rows' coefficients (as in cof_passk)
+  cd E[RK][NC];
+  for (int q = 0; q < n; q++)
+    for (int v = 0; v < RK; v++) E[v][q] = make_double2(0.0, 0.0);
+  cd s = make_double2(0.0, 0.0);
+  for (int c = 0; c < kW; c++) {
+    const int m = mem0 + c;
+    const cd g = Dets[dix(c, f, kmax, T, tid)];
+    const cd* r[RK];
+    for (int u = 0; u < RK; u++) r[u] = S + (size_t)a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + u] * L;
+    cd D[RK][RK];
+    for (int u = 0; u < RK; u++)
+      for (int v = 0; v < RK; v++) D[u][v] = make_double2(0.0, 0.0);
+    for (int q = 0; q < n; q++)
+      for (int u = 0; u < RK; u++) {
+        const cd b = dev::ldS(r[u] + col[q]);
+        for (int v = 0; v < RK; v++) D[u][v] = dev::cfma(b, Y[(size_t)(v * n + q) * T], D[u][v]);
+      }
+    cd adj[RK][RK], dd;
+    adjugate<RK>(D, adj, &dd);
+    s = dev::cfma(g, dd, s);
+    cd ga[RK][RK];
+    for (int u = 0; u < RK; u++)
+      for (int v = 0; v < RK; v++) ga[u][v] = dev::cmul(g, adj[u][v]);
+    for (int q = 0; q < n; q++)
+      for (int u = 0; u < RK; u++) {
+        const cd b = dev::ldS(r[u] + col[q]);
+        for (int v = 0; v < RK; v++) E[v][q] = dev::cfma(b, ga[v][u], E[v][q]);
+      }
+    cd* Rc = R + (size_t)c * RK * RK * T + tid;
+    for (int u = 0; u < RK; u++)
+      for (int v = 0; v < RK; v++) Rc[(size_t)(u * RK + v) * T] = dev::cmul(sd, ga[v][u]);
+  }
+  // shared rows: row rp[i] = sd [ s u~ - sum_v (u~ . E_v) z'_v ], u~ = A1'^{-1} e_{rp[i]} at
+  // the pivot columns
+  const cd ss = dev::cmul(sd, s);
+  for (int i = 0; i < M; i++) {
+    cd u[MC];
+    for (int p = 0; p < M; p++) {
+      if (p < i) {
+        u[p] = make_double2(0.0, 0.0);
+      } else if (p == i) {
+        u[p] = make_double2(1.0, 0.0);
+      } else {
+        cd w = dev::cneg(A[p][i]);
+        for (int t = i + 1; t < p; t++) w = dev::cfms(A[p][t], u[t], w);
+        u[p] = w;
+      }
+    }
+    for (int p = M - 1; p >= 0; p--) {
+      cd w = u[p];
+      for (int t = p + 1; t < M; t++) w = dev::cfms(A[p][t], u[t], w);
+      u[p] = dev::cmul(w, rc[p]);
+    }
+    cd se[RK];
+    for (int v = 0; v < RK; v++) {
+      cd e = make_double2(0.0, 0.0);
+      for (int t = 0; t < M; t++) e = dev::cfma(u[t], E[v][cp[t]], e);
+      se[v] = dev::cmul(sd, e);
+    }
+    cd* row = Mst + (size_t)rp[i] * n;
+    for (int q = 0; q < n; q++) {
+      cd x = make_double2(0.0, 0.0);
+      for (int v = 0; v < RK; v++) x = dev::cfms(se[v], Y[(size_t)(v * n + q) * T], x);
+      row[q] = x;
+    }
+    for (int t = 0; t < M; t++) row[cp[t]] = dev::cfma(ss, u[t], row[cp[t]]);
+  }
+}
+
+template <int NC, int RK>
+__device__ __noinline__ bool cof_passk(const FwdArgs& a, int f, int n, int mem0, int kW, int tid,
                                        int T, int kmax, const int32_t* __restrict__ col,
                                        const int32_t* __restrict__ arow, const cd* Dets, const cd* Y,
                                        bool guarded, cd* Mst, cd* R) {
   const int M = n - RK;
   const cd* S = a.S[f];
   const int L = a.L_f[f];
+  if (guarded) return false;  // the forward's shared-row factorisation failed its pivot guard
   const cd sd = Y[(size_t)RK * n * T];
   cd E[RK][NC];
   for (int q = 0; q < n; q++)
@@ -439,7 +625,7 @@ __device__ __noinline__ void cof_passk(const FwdArgs& a, int f, int n, int mem0,
     for (int u = 0; u < RK; u++)
 #pragma unroll
       for (int v = 0; v < RK; v++)
-        Rc[(size_t)(u * RK + v) * T] = guarded ? make_double2(0.0, 0.0) : dev::cmul(sd, ga[v][u]);
+        Rc[(size_t)(u * RK + v) * T] = dev::cmul(sd, ga[v][u]);
   }
   // LU of A1 (the shared rows on the first n - k columns), partial pivoting
   constexpr int MC = NC - RK > 0 ? NC - RK : 1;
@@ -484,13 +670,7 @@ __device__ __noinline__ void cof_passk(const FwdArgs& a, int f, int n, int mem0,
       for (int q = k + 1; q < M; q++) A[i][q] = dev::cfms(l, A[k][q], A[i][q]);
     }
   }
-  if (guarded || (M > 0 && (zero || emax - emin > a.kp))) {
-    atomicOr(&a.counters[0], kStatusUnsupported);
-    for (int e = 0; e < M * n; e++) Mst[e] = make_double2(0.0, 0.0);
-    for (int c = 0; c < kW; c++)
-      for (int t = 0; t < RK * RK; t++) R[((size_t)c * RK * RK + t) * T + tid] = make_double2(0.0, 0.0);
-    return;
-  }
+  if (M > 0 && (zero || emax - emin > a.kp)) return false;  // A1 fails the guard: cof_passk_guarded
   const cd ss = dev::cmul(sd, s);
   for (int i = 0; i < M; i++) {  // u = column perm[i] of A1^{-1} = U^{-1} L^{-1} e_i
     cd u[MC];
@@ -527,6 +707,7 @@ __device__ __noinline__ void cof_passk(const FwdArgs& a, int f, int n, int mem0,
 #pragma unroll
     for (int v = 0; v < RK; v++) row[M + v] = dev::cneg(se[v]);  // z_v's unit coordinates
   }
+  return true;
 }
 
 // Scatter of one warp's sinks for a family of rank k (flavour f): lane s owns row s -- a
@@ -896,10 +1077,16 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
           cd* Rk = B.r2 + (size_t)cta * B.kmax * B.rk2 * T;
           const cd* Yf = Ysm + (size_t)a.yoff[f] * T + tid;
           const bool gd = (pguard >> f) & 1;
+          // a shared-row factorisation that fails the pivot guard is redone with complete
+          // pivoting (or signed minors for exactly dependent shared rows)
           if (rho == 2) {
-            cof_passk<NCMAX, 2>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk);
+            if (!cof_passk<NCMAX, 2>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk))
+              cof_passk_guarded<NCMAX, 2>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets,
+                                          const_cast<cd*>(Yf), myStage, Rk);
           } else if constexpr (NCMAX >= 14) {
-            cof_passk<NCMAX, 3>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk);
+            if (!cof_passk<NCMAX, 3>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk))
+              cof_passk_guarded<NCMAX, 3>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets,
+                                          const_cast<cd*>(Yf), myStage, Rk);
           }
           __syncwarp();
           const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);

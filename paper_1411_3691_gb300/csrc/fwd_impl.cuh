@@ -35,34 +35,45 @@ __device__ __forceinline__ unsigned long long fresh_flops(int n) {
   return (unsigned long long)(m * (m + 1) / 2 + 6 * (m - 1) + 3 * m * (m - 1) +
                               8 * (m - 1) * m * (2 * m - 1) / 6 + 6 * (m - 1));
 }
-// ... the part of a grouped refactor (group_fresh) that the group shares: pivot search,
-// reciprocal, multipliers and updates of the first n - 1 columns, product of their pivots ...
-__device__ __forceinline__ unsigned long long group_shared_flops(int n) {
+// ... and a grouped refactor (group_fresh) of pairs whose matrices share their first
+// n - rc columns: the group's elimination of those columns and the rows of L^{-1} P of the
+// rc remaining rows (one complex multiply-add per unused row and step) ...
+__device__ __forceinline__ unsigned long long group_shared_flops(int n, int rc) {
   long long f = 0;
-  for (int k = 0; k + 1 < n; k++) f += (n - k) + 6 + 6 * (n - k - 1) + 8 * (n - k - 1) * (n - 2 - k);
-  return (unsigned long long)(f + 6 * (n > 2 ? n - 2 : 0));
+  const int M = n - rc;
+  for (int k = 0; k < M; k++)
+    f += (n - k) + 6 + 6 * (n - k - 1) + 8 * (n - k - 1) * (M - 1 - k) + 8 * rc * (n - k - 1);
+  return (unsigned long long)(f + 6 * (M > 1 ? M - 1 : 0));
 }
-// ... and the part of each pair of the group: its last column through the n - 1 steps,
-// the last pivot's measure and the product with it.
-__device__ __forceinline__ unsigned long long group_pair_flops(int n) {
-  return (unsigned long long)(4LL * n * (n - 1) + 1 + 6);
+// ... and each pair's share: rc x rc dot products of length n, the last rc x rc step (for
+// rc = 2: two pivot measures, a reciprocal, a multiplier, one update, two products) and
+// the product with the shared pivots.
+__device__ __forceinline__ unsigned long long group_pair_flops(int n, int rc) {
+  return (unsigned long long)(rc * rc * (8LL * n - 2) + (rc == 2 ? 2 + 6 + 6 + 8 + 12 : 6));
 }
 
 // Fresh determinants of a group of queued pairs that share member m and a two-sided sink
-// family Q with one changed column (flavour f; family of rank rho): their matrices agree in
-// the first n - 1 columns (the family's n - rho shared rows and the member's rho rows, in
-// member_rows order, against the sink family's shared columns) and differ in the last.  Partial-pivot LU eliminates column by column, so
-// the pivots and multipliers of the first n - 1 columns are common to the group: the warp
-// factorises them once (lane i holds row i), then every lane of the group carries its own
-// sink's last column through the same steps -- the arithmetic of a fresh LU per pair at
-// O(n^2) per pair instead of O(n^3).  Called by the whole warp; returns the determinant on
-// the lanes in grp.
-template <int NC>
+// family Q whose members change RC columns of flavour f (RC = 1 or 2; family of rank rho):
+// their matrices G = [R | A_j] agree in the first n - RC columns R (the family's n - rho
+// shared rows and the member's rho rows, in member_rows order, against the sink family's
+// shared columns) and differ in the last RC columns A_j.  Partial-pivot LU eliminates
+// column by column, so the first n - RC steps are those of R for every pair: P R = L [U; 0],
+// and the last RC rows of L^{-1} P A_j form the RC x RC block that the last steps factorise,
+// det G = sign(P) det(U) det(V A_j) with V the rows of L^{-1} P that belong to the RC rows
+// left after the shared steps.  The warp factorises R once (lane i holds row i and keeps
+// its multiplier of every step), forms V by walking the steps backwards (the coefficient of
+// a step's pivot row is minus the warp sum, over the rows still unused at that step, of
+// multiplier times coefficient), and each lane of the group then needs RC x RC dot products
+// of length n with its own sink's columns and the last RC x RC step with the same pivot
+// rule.  Called by the whole warp; returns the determinant on the lanes in grp.
+template <int NC, int RC>
 __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, int rho, int m, int Q,
                                                int64_t j, unsigned grp) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int NR = NC - RC > 0 ? NC - RC : 1;
   const int lane = threadIdx.x & 31;
   const int n = a.n_f[f];
+  const int M = n - RC;  // shared columns: the common elimination steps
   const int L = a.L_f[f];
   const dev::cd* S = a.S[f];
   const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
@@ -70,27 +81,19 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   // label of row i: the family's shared rows, then the member's changed rows
   auto row_label = [&](int i) { return i < n - rho ? arow[i] : mlab[min(i - (n - rho), rho - 1)]; };
-  // lane i < n: row i of the n x (n - 1) block
-  const int rlab = row_label(lane);
-  dev::cd R[NC];
+  const int rlab = row_label(min(lane, n - 1));
+  dev::cd R[NR];
 #pragma unroll
-  for (int u = 0; u < NC - 1; u++)
-    R[u] = (lane < n && u < n - 1) ? dev::ldS(S + (size_t)rlab * L + scol[u]) : make_double2(0.0, 0.0);
-  // this lane's sink: its last column, entries in row order 0..n-1
-  const bool mine = (grp >> lane) & 1;
-  dev::cd c[NC];
-  const int lc = mine ? dev::sink_cols(a, j)[a.off_f[f] + n - 1] : 0;
-#pragma unroll
-  for (int i = 0; i < NC; i++) {
-    c[i] = (mine && i < n) ? dev::ldS(S + (size_t)row_label(i) * L + lc) : make_double2(0.0, 0.0);
-  }
-  unsigned piv = 0;  // rows already used as pivots
+  for (int u = 0; u < NR; u++)
+    R[u] = (lane < n && u < M) ? dev::ldS(S + (size_t)rlab * L + scol[u]) : make_double2(0.0, 0.0);
+  unsigned piv = 0;     // rows already used as pivots
+  int mystep = NC;      // the step at which this lane's row became the pivot (NC: never)
   int parity = 0;
   bool zero = false;
   dev::cd det = make_double2(1.0, 0.0);
 #pragma unroll
-  for (int k = 0; k < NC - 1; k++) {
-    if (k >= n - 1) break;
+  for (int k = 0; k < NR; k++) {
+    if (k >= M) break;
     // pivot: the largest |re| + |im| in column k among the unused rows, lowest row on ties
     const bool cand = lane < n && !((piv >> lane) & 1);
     double best = cand ? dev::abs1(R[k]) : -1.0;
@@ -107,37 +110,83 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
     // the permutation's parity: p moves ahead of the unused rows that precede it
     parity ^= __popc(~piv & ((1u << p) - 1u) & ((1u << n) - 1u)) & 1;
     piv |= 1u << p;
+    mystep = lane == p ? k : mystep;
     zero |= best == 0.0;
     const dev::cd pk = make_double2(__shfl_sync(FULL, R[k].x, p), __shfl_sync(FULL, R[k].y, p));
     det = (k == 0) ? pk : dev::cmul(det, pk);
     const dev::cd rc = dev::crcp(pk);
-    // multipliers of the unused rows; the group's last columns follow
     const bool act = lane < n && !((piv >> lane) & 1);
     const dev::cd l = dev::cmul(R[k], rc);
 #pragma unroll
-    for (int u = k + 1; u < NC - 1; u++) {
-      if (u >= n - 1) break;
+    for (int u = k + 1; u < NR; u++) {
+      if (u >= M) break;
       const dev::cd pu = make_double2(__shfl_sync(FULL, R[u].x, p), __shfl_sync(FULL, R[u].y, p));
       if (act) R[u] = dev::cfms(l, pu, R[u]);
     }
-    // last column of each sink: row i -= l_i * (pivot row's entry)
-    dev::cd vp = c[0];
+    if (act) R[k] = l;  // this row's multiplier of step k
+  }
+  // the RC rows left after the shared steps, ascending
+  const unsigned rest = ~piv & ((1u << n) - 1u);
+  int left[RC];
+  left[0] = __ffs(rest) - 1;
+  if (RC == 2) left[RC - 1] = __ffs(rest & ~(1u << left[0])) - 1;
+  // V: lane i holds the coefficient of row i in each remaining row's functional
+  dev::cd V[RC];
 #pragma unroll
-    for (int i = 1; i < NC; i++) vp = i == p ? c[i] : vp;
+  for (int t = 0; t < RC; t++) V[t] = make_double2(lane == left[t] ? 1.0 : 0.0, 0.0);
 #pragma unroll
-    for (int i = 0; i < NC; i++) {
-      if (i >= n) break;
-      const dev::cd li = make_double2(__shfl_sync(FULL, l.x, i), __shfl_sync(FULL, l.y, i));
-      if (!((piv >> i) & 1)) c[i] = dev::cfms(li, vp, c[i]);
+  for (int k = NR - 1; k >= 0; k--) {
+    if (k >= M) continue;
+    const int p = __ffs(__ballot_sync(FULL, mystep == k)) - 1;
+    const bool unused = lane < n && mystep > k;
+#pragma unroll
+    for (int t = 0; t < RC; t++) {
+      double2 sum = unused ? dev::cmul(R[k], V[t]) : make_double2(0.0, 0.0);
+      sum = dev::warp_sum(sum);
+      if (lane == p) V[t] = dev::cneg(sum);
     }
   }
-  // the remaining row holds the last pivot
-  const int last = __ffs(~piv & ((1u << n) - 1u)) - 1;
-  dev::cd vl = c[0];
+  // each lane: its sink's last RC columns against the RC functionals
+  const bool mine = (grp >> lane) & 1;
+  const int32_t* cj = dev::sink_cols(a, j) + a.off_f[f];
+  dev::cd D[RC][RC];
 #pragma unroll
-  for (int i = 1; i < NC; i++) vl = i == last ? c[i] : vl;
-  zero |= __double_as_longlong(dev::abs1(vl)) == 0;
-  det = n == 1 ? vl : dev::cmul(det, vl);
+  for (int t = 0; t < RC; t++)
+#pragma unroll
+    for (int u = 0; u < RC; u++) D[t][u] = make_double2(0.0, 0.0);
+  int lc[RC];
+#pragma unroll
+  for (int u = 0; u < RC; u++) lc[u] = mine ? cj[n - RC + u] : 0;
+#pragma unroll
+  for (int i = 0; i < NC; i++) {
+    if (i >= n) break;
+    const int li = row_label(i);
+    dev::cd vi[RC];
+#pragma unroll
+    for (int t = 0; t < RC; t++) vi[t] = make_double2(__shfl_sync(FULL, V[t].x, i), __shfl_sync(FULL, V[t].y, i));
+#pragma unroll
+    for (int u = 0; u < RC; u++) {
+      const dev::cd x = mine ? dev::ldS(S + (size_t)li * L + lc[u]) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int t = 0; t < RC; t++) D[t][u] = dev::cfma(vi[t], x, D[t][u]);
+    }
+  }
+  if (RC == 1) {
+    zero |= __double_as_longlong(dev::abs1(D[0][0])) == 0;
+    det = M == 0 ? D[0][0] : dev::cmul(det, D[0][0]);
+  } else {
+    // last 2 x 2 step: pivot the larger |re| + |im| of the first column, ties to the lower row
+    const double b0 = dev::abs1(D[0][0]), b1 = dev::abs1(D[RC - 1][0]);
+    const bool swp = dev::gt_nonneg(b1, b0);
+    parity ^= (int)swp;
+    const dev::cd pv = swp ? D[RC - 1][0] : D[0][0], ov = swp ? D[0][0] : D[RC - 1][0];
+    const dev::cd pw = swp ? D[RC - 1][RC - 1] : D[0][RC - 1], ow = swp ? D[0][RC - 1] : D[RC - 1][RC - 1];
+    zero |= __double_as_longlong(swp ? b1 : b0) == 0;
+    const dev::cd l = dev::cmul(ov, dev::crcp(pv));
+    const dev::cd last = dev::cfms(l, pw, ow);
+    zero |= __double_as_longlong(dev::abs1(last)) == 0;
+    det = M == 0 ? dev::cmul(pv, last) : dev::cmul(dev::cmul(det, pv), last);
+  }
   if (zero) return make_double2(0.0, 0.0);
   return parity ? dev::cneg(det) : det;
 }
@@ -160,22 +209,25 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
     const bool need = have && ((e.fail >> f) & 1);
     const int n = a.n_f[f];
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
-    const bool grouped = need && NCMAX <= 18 && n >= 2 && Q >= 0 && a.q_two[Q] &&
-                         a.q_rank[(int64_t)Q * a.F + f] == 1;
-    unsigned todo = __ballot_sync(FULL, grouped);
+    const int sig = (Q >= 0 && a.q_two[Q]) ? a.q_rank[(int64_t)Q * a.F + f] : 0;
+    const bool grouped = need && NCMAX <= 18 && n >= 2 && sig == 1;
+    const bool grouped2 = need && NCMAX <= 18 && n >= 3 && sig == 2;
+    unsigned todo = __ballot_sync(FULL, grouped || grouped2);
     while (todo) {
       const int leader = __ffs(todo) - 1;
       const int lm = __shfl_sync(FULL, have ? e.member : 0, leader);
       const int lq = __shfl_sync(FULL, Q, leader);
+      const int lsig = __shfl_sync(FULL, sig, leader);
       const unsigned grp = __ballot_sync(FULL, ((todo >> lane) & 1) && e.member == lm && Q == lq);
-      const double2 d = group_fresh<NCMAX <= 18 ? NCMAX : 18>(a, W, f, rho, lm, lq, j, grp);
+      const double2 d = lsig == 1 ? group_fresh<NCMAX <= 18 ? NCMAX : 18, 1>(a, W, f, rho, lm, lq, j, grp)
+                                  : group_fresh<NCMAX <= 18 ? NCMAX : 18, 2>(a, W, f, rho, lm, lq, j, grp);
       if ((grp >> lane) & 1) {
         prod = dev::cmul(prod, d);
-        rflops += group_pair_flops(n) + (lane == leader ? group_shared_flops(n) : 0ull);
+        rflops += group_pair_flops(n, lsig) + (lane == leader ? group_shared_flops(n, lsig) : 0ull);
       }
       todo &= ~grp;
     }
-    if (need && !grouped) {
+    if (need && !grouped && !grouped2) {
       dev::member_rows(a, W, e.member, f, rho, rows);
       const double2 d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, cols + a.off_f[f]);
       prod = dev::cmul(prod, d);

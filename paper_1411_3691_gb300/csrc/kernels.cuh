@@ -16,7 +16,7 @@ enum : unsigned long long {
   kStatusNonFinite = 1ull,
   kStatusBadIndex = 2ull,
   kStatusTimeout = 4ull,
-  kStatusUnsupported = 8ull,  // a two-row family's shared rows failed the pivot guard in the adjoint
+  kStatusUnsupported = 8ull,  // reserved: a request the kernels could not complete
 };
 
 // Everything one forward evaluation of one plan needs on the device.

@@ -363,8 +363,7 @@ mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream) {
     return MHC_EINVAL;
   }
   if (c[0] & kStatusUnsupported) {
-    set_error("the adjoint met a two-row family whose shared rows fail the pivot guard; its "
-              "gradient is left out: plan with opts.rank2 = 0");
+    set_error("a kernel could not complete a request it does not support");
     return MHC_EUNSUPPORTED;
   }
   if (c[0] & kStatusNonFinite) {

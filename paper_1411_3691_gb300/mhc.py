@@ -31,7 +31,8 @@ EXPORTED = ["mhc_last_error", "mhc_plan_opts_default", "mhc_plan", "mhc_plan_des
             "mhc_correlator_cw",
             "mhc_correlator_backward",
             "mhc_pair_dets", "mhc_get_status", "mhc_batch_create", "mhc_batch_destroy",
-            "mhc_batch_correlator", "mhc_batch_info", "mhc_fp64_peak", "mhc_complex_reciprocal"]
+            "mhc_batch_correlator", "mhc_batch_info", "mhc_batch_shape", "mhc_tune_cache_get",
+            "mhc_tune_cache_put", "mhc_fp64_peak", "mhc_complex_reciprocal"]
 
 
 class MHCError(RuntimeError):
@@ -98,6 +99,9 @@ def lib():
         L.mhc_batch_destroy.restype = None
         L.mhc_batch_correlator.argtypes = [_vp, ctypes.POINTER(ctypes.POINTER(_vp)), ctypes.POINTER(_vp), _vp]
         L.mhc_batch_info.argtypes = [_vp, _i32p, _i32p]
+        L.mhc_batch_shape.argtypes = [_vp, _i32p, _i32p, _f64p]
+        L.mhc_tune_cache_get.argtypes = [ctypes.c_char_p, _i32p]
+        L.mhc_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_int32]
         L.mhc_fp64_peak.argtypes = [ctypes.c_int32, _f64p, _vp]
         L.mhc_complex_reciprocal.argtypes = [ctypes.c_int64, _vp, _vp, _vp]
         for name in EXPORTED:
@@ -299,6 +303,26 @@ def mhc_batch_info(batch):
     n = ctypes.c_int32()
     _check(lib().mhc_batch_info(_vp(batch), ctypes.byref(t), ctypes.byref(n)))
     return t.value, n.value
+
+
+def mhc_batch_shape(batch):
+    """Per n class (n_f <= 8, <= 18, <= 32): chosen sink tiles, whether each came from the
+    tuning cache, and the timed candidates (ms at tiles 32, 64, 128)."""
+    tiles = (ctypes.c_int32 * 3)()
+    cached = (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_double * 9)()
+    _check(lib().mhc_batch_shape(_vp(batch), tiles, cached, ms))
+    return list(tiles), list(cached), [list(ms[3 * c:3 * c + 3]) for c in range(3)]
+
+
+def mhc_tune_cache_get(key: str) -> int:
+    t = ctypes.c_int32()
+    _check(lib().mhc_tune_cache_get(key.encode(), ctypes.byref(t)))
+    return t.value
+
+
+def mhc_tune_cache_put(key: str, tile: int) -> None:
+    _check(lib().mhc_tune_cache_put(key.encode(), tile))
 
 
 def mhc_fp64_peak(iters: int = 200000, stream=None) -> float:

@@ -57,6 +57,39 @@ def test_batch_matches_oracle_and_plain(M):
     M.mhc_batch_destroy(batch)
 
 
+def test_tuning_cache_second_create(M, tmp_path, monkeypatch):
+    """A second mhc_batch_create with the same plans takes every class's tile from the
+    tuning cache (no timing), chooses the same tiles, and gives bitwise the same results."""
+    monkeypatch.setenv("MHC_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    items = [wl.batch_item(b, max_terms=900) for b in range(12)]
+    plans = [M.Plan.from_workload(w) for w in items]
+    S = [[torch.from_numpy(s).cuda() for s in w.S] for w in items]
+    res = []
+    for rep in range(2):
+        batch = M.mhc_batch_create([p.handle for p in plans])
+        tiles, cached, ms = M.mhc_batch_shape(batch)
+        used = [c for c in range(3) if tiles[c]]
+        assert len(used) >= 2
+        assert all(tiles[c] in (32, 64, 128) for c in used)
+        if rep == 0:
+            assert all(cached[c] == 0 and max(ms[c]) > 0 for c in used)
+        else:
+            assert all(cached[c] == 1 for c in used) and tiles == res[0][0]
+        outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in items]
+        M.mhc_batch_correlator(batch, S, outs)
+        torch.cuda.synchronize()
+        res.append((tiles, [o.cpu().numpy().tobytes() for o in outs]))
+        M.mhc_batch_destroy(batch)
+    assert res[0][1] == res[1][1]
+    for k, w in enumerate(items[:4]):
+        ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+        got = complex(*np.frombuffer(res[1][1][k], dtype=np.float64))
+        assert abs(got - ref) <= 1e-11 * scale
+    for p in plans:
+        M.mhc_get_status(p.handle)
+        p.close()
+
+
 def test_full_batch_64_correlators(M):
     """The 64-correlator batch of the benchmark in its launch configuration (autotuned
     shape, per-class persistent kernels, CUDA graph), every correlator against the oracle

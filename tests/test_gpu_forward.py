@@ -251,3 +251,34 @@ def test_forced_members_in_multi_row_families(M, three_row_frac):
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
     assert plan.stats()["refactor_child"] >= len(forced) * len(w.w_snk) // 2
     plan.close()
+
+
+def test_forced_members_against_two_column_sink_families(M):
+    """Near-singular members (a row set to the near-twin of a shared row) against sink
+    families that change two columns: the pairs of one member and one such sink family agree
+    in all but their last two columns and are refactored together (the shared elimination of
+    the first n - 2 columns once, then each sink's two columns and the last 2 x 2 step).  C
+    against the oracle, the refactors counted, and the refactor flops below a fresh LU per
+    refactored pair and flavour."""
+    a = wl.make_workload("f2c", [18, 12], [96, 60], [32, 32, 32], [32, 32, 32, 7], diag=3.0, seed=81,
+                         two_row_frac=0.0, forced_frac=0.2, twins=8)
+    b = wl.make_workload("f2c", [18, 12], [96, 60], [32, 32, 32], [32, 32, 32, 7], diag=3.0, seed=81,
+                         two_row_frac=1.0, forced_frac=0.2, twins=8)
+    assert all(np.array_equal(x, y) for x, y in zip(a.S, b.S))
+    w = wl.Workload("f2c", a.n_f, a.S, a.labels_src, a.w_src, b.labels_snk, b.w_snk, a.meta)
+    plan = M.Plan.from_workload(w)
+    sinks = plan.sinks()
+    assert sinks["two_sided"].sum() >= 3
+    C, plan, S = gpu_C(M, w, plan=plan)
+    st = plan.stats()
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    st = plan.stats()
+    forced = w.meta["src"]["forced"]
+    assert len(forced) > 0
+    n_ref = st["refactor_parent"] + st["refactor_child"]
+    assert n_ref >= len(forced) * len(w.w_snk) // 2
+    fresh18 = 18 * 19 / 2 + 6 * 17 + 3 * 18 * 17 + 8 * 17 * 18 * 35 / 6 + 6 * 17
+    assert 0 < st["refactor_flops"] < 0.5 * n_ref * fresh18
+    plan.close()
