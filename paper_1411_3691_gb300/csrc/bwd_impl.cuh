@@ -308,12 +308,34 @@ __device__ __forceinline__ void two_cof(int n_rt, const cd* __restrict__ Binv, c
   }
 }
 
+// Compact form of two_cof for the scatter: alpha = h . y and eta = h[0..M) B^{-1} (written
+// to Mst[0] and Mst[1 + m]); the scatter forms cof[m][q] = alpha B^{-1}[q][m] - eta_m y_q
+// (q < M) and cof[m][M] = -det(B) eta_m itself, so a sink stages M + 1 values, not M n.
+template <int NC, int NFIX>
+__device__ __forceinline__ void two_eta(int n_rt, const cd* __restrict__ Binv, const cd* h,
+                                        const cd* __restrict__ Y, int ys, cd* Mst) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 1;
+  cd alpha = dev::cmul(h[0], Y[0]);
+#pragma unroll UNR
+  for (int q = 1; q < n; q++) alpha = dev::cfma(h[q], Y[q * ys], alpha);
+  Mst[0] = alpha;
+#pragma unroll UNR
+  for (int m = 0; m < M; m++) {
+    cd eta = make_double2(0.0, 0.0);
+#pragma unroll UNR
+    for (int q = 0; q < M; q++) eta = dev::cfma(h[q], __ldg(Binv + q * M + m), eta);
+    Mst[1 + m] = eta;
+  }
+}
+
 // Pass 2 of one (sink, flavour): the aggregated member row h = sum_c gamma_c g_c and the
 // shared-row cofactors of [A; h] into Mst (row-major M x n) -- from B^{-1} for a two-sided
 // block, from the recomputed shared-row LU otherwise, from signed minors where the pivot
 // guard fired.  With NFIX the row h stays in registers.
 template <int NC, int NFIX>
-__device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n_rt, int W,
+__device__ __forceinline__ int cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n_rt, int W,
                                          int mem0, int kW, double wj, int tid, int T,
                                          const int32_t* __restrict__ col, const int32_t* __restrict__ arow,
                                          const cd* Dets, const cd* Y, bool guarded, const cd* Binv,
@@ -332,21 +354,19 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
 #pragma unroll UNR
     for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
   }
-  bool ok = false;
-  if (!guarded) {
-    if (Binv) {
-      two_cof<NC, NFIX>(n, Binv, detB, h, Y, T, Mst);
-      ok = true;
-    } else {
-      ok = lu_block<NC, NFIX>(S, L, n, arow, col, h, Mst, a.kp);
-    }
+  if (!guarded && Binv) {
+    two_eta<NC, NFIX>(n, Binv, h, Y, T, Mst);
+    return 1;
   }
+  bool ok = false;
+  if (!guarded) ok = lu_block<NC, NFIX>(S, L, n, arow, col, h, Mst, a.kp);
   if (!ok) {
     cd hl[NC];
 #pragma unroll UNR
     for (int q = 0; q < n; q++) hl[q] = h[q];
     minors_block<NC>(S, L, n, arow, col, hl, const_cast<cd*>(Y), T, Mst);
   }
+  return 0;
 }
 
 // Family of rank k (k = 2, 3 changed rows), shared rows A ((n-k) x n), member rows
@@ -794,7 +814,7 @@ __device__ __noinline__ void scatter_rowsk(const FwdArgs& a, const BwdArgs& B, i
 }
 
 template <int NCMAX>
-__device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n, int W,
+__device__ __forceinline__ int dispatch_cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n, int W,
                                                   int mem0, int kW, double wj, int tid, int T,
                                                   const int32_t* col, const int32_t* arow, const cd* Dets,
                                                   const cd* Y, bool guarded, const cd* Binv, cd detB,
@@ -802,14 +822,14 @@ __device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArg
 #define MHC_COF(NN) cof_pass<NN, NN>(a, B, f, NN, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, \
                                      Binv, detB, Mst)
   switch (n) {
-    case 1: MHC_COF(1); return;
-    case 2: MHC_COF(2); return;
-    case 3: MHC_COF(3); return;
-    case 4: MHC_COF(4); return;
-    case 5: MHC_COF(5); return;
-    case 6: MHC_COF(6); return;
+    case 1: return MHC_COF(1);
+    case 2: return MHC_COF(2);
+    case 3: return MHC_COF(3);
+    case 4: return MHC_COF(4);
+    case 5: return MHC_COF(5);
+    case 6: return MHC_COF(6);
     default:
-      cof_pass<NCMAX, 0>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, Binv, detB, Mst);
+      return cof_pass<NCMAX, 0>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, Binv, detB, Mst);
   }
 #undef MHC_COF
 }
@@ -832,7 +852,7 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
                                              int kW, int mem0, int nlive, int T, int warp, int lane,
                                              const int32_t* __restrict__ mycol, int myQ, int mynsh,
                                              const cd* Stage, const cd* Ysm,
-                                             const cd* Dets, cd* Df) {
+                                             const cd* Dets, cd* Df, int W, int mymode) {
   constexpr int UNR = NFIX ? NC : 1;
   constexpr unsigned FULL = 0xffffffffu;
   const int n = NFIX ? NFIX : n_rt;
@@ -871,6 +891,7 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
         const int Qj = __shfl_sync(FULL, myQ, src);
         const int nsj = __shfl_sync(FULL, mynsh, src);
         const int rep = __shfl_sync(FULL, myrep, src);
+        const int modej = __shfl_sync(FULL, mymode, src);
         int lab = 0;  // the label of this cell's column in sink jl
 #pragma unroll UNR
         for (int p = 0; p < n; p++) {
@@ -895,7 +916,24 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
         }
         const int ts = warp * 32 + jl;
         const cd g = (mem && !decltype(sh)::value) ? Dets[dix(c, f, B.kmax, T, ts)] : make_double2(1.0, 0.0);
-        const cd v = mem ? Ycol[ts] : Stage[(size_t)ts * B.mn_max + s * n + q];
+        cd v;
+        if (mem) {
+          v = Ycol[ts];
+        } else if (modej) {
+          // compact staging of a two-sided block: alpha B^{-1}[q][s] - eta_s y_q, or
+          // -det(B) eta_s for the changed column
+          const cd* st = Stage + (size_t)ts * B.mn_max;
+          const int64_t wq = (int64_t)W * a.n_q + Qj;
+          const cd eta = st[1 + s];
+          if (q < M) {
+            const cd bi = __ldg(B.kinv + wq * B.kistride + B.kioff[f] + q * M + s);
+            v = dev::cfms(eta, Ycol[ts], dev::cmul(st[0], bi));
+          } else {
+            v = dev::cneg(dev::cmul(__ldg(a.kbuf + wq * a.kstride + a.koff[f] + M * M + M + 1), eta));
+          }
+        } else {
+          v = Stage[(size_t)ts * B.mn_max + s * n + q];
+        }
         const bool shcol = q < nsh;
         if (!rep) {
           // one complex FMA (an addition in a step of shared rows) per lane, on the register
@@ -931,9 +969,10 @@ template <int NCMAX>
 __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs& B, int f, int n,
                                                  int kW, int mem0, int nlive, int T, int warp, int lane,
                                                  const int32_t* mycol, int myQ, int mynsh,
-                                                 const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
+                                                 const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df,
+                                                 int W, int mymode) {
 #define MHC_SC(NN) scatter_rows<NN, NN>(a, B, f, NN, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, \
-                                        Stage, Ysm, Dets, Df)
+                                        Stage, Ysm, Dets, Df, W, mymode)
   switch (n) {
     case 1: MHC_SC(1); return;
     case 2: MHC_SC(2); return;
@@ -943,7 +982,7 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
     case 6: MHC_SC(6); return;
     default:
       scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, Stage, Ysm,
-                             Dets, Df);
+                             Dets, Df, W, mymode);
   }
 #undef MHC_SC
 }
@@ -1110,7 +1149,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       // B^{-1} shared by the (family, sink family) block
       const cd* Binv = twoc ? B.kinv + wq * B.kistride + B.kioff[f] : nullptr;
       const cd detB = twoc ? a.kbuf[wq * a.kstride + a.koff[f] + M * M + M + 1] : make_double2(0.0, 0.0);
-      dispatch_cof_pass<NCMAX>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets,
+      const int mymode = dispatch_cof_pass<NCMAX>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets,
                                Ysm + (size_t)a.yoff[f] * T + tid, (pguard >> f) & 1, Binv, detB, myStage);
       __syncwarp();
 
@@ -1120,7 +1159,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
       const int nlive = rem < 32 ? (int)rem : 32;
       dispatch_scatter<NCMAX>(a, B, f, n, kW, mem0, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh,
-                              Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax);
+                              Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax, W, mymode);
       __syncwarp();
     }
   }

@@ -404,8 +404,11 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   }
 }
 
+// Registers: the n <= 8 class keeps 168 (12 one-warp blocks per SM, or 3 blocks of its
+// 128-thread tile); the larger classes may use all 255, measured fastest for n = 18 (8 blocks
+// per SM against 9 at 216 and 10 at 200, whose spills cost more than the warps gain).
 template <int NCMAX>
-__global__ void __launch_bounds__(128) fwd_kernel(const FwdArgs a) {
+__global__ void __maxnreg__(NCMAX <= 8 ? 168 : 255) fwd_kernel(const FwdArgs a) {
   extern __shared__ double2 smem[];
   const int64_t item = a.item0 + blockIdx.x;
   const int64_t pos = item / a.n_tiles;
