@@ -60,7 +60,7 @@ typedef enum {
 
 #define MHC_NMAX 32     /* largest n_f (quarks of one flavour in a term) */
 #define MHC_FMAX 8      /* largest number of flavours */
-#define MHC_MAX_RANK 3  /* most changed rows per family and flavour (stride of the
+#define MHC_MAX_RANK 6  /* most changed rows per family and flavour (stride of the
                            changed-row tables of mhc_plan_families) */
 
 /* Planner options.  mhc_plan_opts_default() fills the defaults listed here. */
@@ -81,9 +81,15 @@ typedef struct {
                           columns (two-sided update).                           0     */
   int32_t rank3;       /* 1 (with rank2): source families may also differ in three
                           rows per flavour with n_f >= 14 (rank-3 update: a 3x3
-                          generalised cofactor with three null vectors; the
-                          general rank-k update of Sec. 5 taken to k = 3).      0     */
-  int32_t reserved[6];
+                          generalised cofactor with three null vectors).        0     */
+  int32_t max_rank;    /* with rank2: the most rows per flavour in which a source
+                          family's members may differ, 2..MHC_MAX_RANK (the rank-k
+                          update of Sec. 5: k null vectors of the shared rows and a
+                          k x k determinant per member); rank k is used for a
+                          flavour with n_f >= 4k + 2 (rank 2: n_f >= 10, rank 3:
+                          n_f >= 14, rank 4: 18, 5: 22, 6: 26).  0: 3 with rank3,
+                          else 2.                                               0     */
+  int32_t reserved[5];
 } mhc_plan_opts;
 
 /* Planner and run statistics. */
@@ -113,7 +119,7 @@ typedef struct {
                                     read by the last mhc_get_status (same counting rule as
                                     flops_per_call; a group of pairs refactored together
                                     counts its shared elimination once)                */
-  int64_t reserved[1];
+  int64_t rank4plus_family_flavours; /* (family, flavour) blocks updated at rank >= 4   */
 } mhc_stats;
 
 /* Thread-local message describing the last failure of this thread's last call. */
@@ -158,14 +164,15 @@ mhc_status mhc_plan_stats(mhc_plan_t plan, mhc_stats* out);
  * Export the work families (host; for inspection and tests).  Pass NULL for the
  * arrays to query the sizes only.  With W = *n_families and Tn = sum_f n_f:
  *   fam_member_offset : int64 [W+1]; members of family w are [off[w], off[w+1])
- *   fam_rank          : int32 [W][F]; 0 (n_f = 0), 1, 2 or 3 changed rows
- *   fam_rows          : int32 [W][F][3]; changed-row positions in the reference tuple
- *                       (ascending; -1 when unused)
+ *   fam_rank          : int32 [W][F]; 0 (n_f = 0), else 1..MHC_MAX_RANK changed rows
+ *   fam_rows          : int32 [W][F][MHC_MAX_RANK]; changed-row positions in the reference
+ *                       tuple (ascending; -1 when unused)
  *   fam_ref           : int32 [W][Tn]; the dominator's labels (reference tuple)
  *   member_term       : int64 [n_src]; source term of each member
  *   member_sign       : int32 [n_src]; +-1: det of the term's own label order equals
  *                       member_sign times prod_f det [shared rows; member rows]
- *   member_labels     : int32 [n_src][F][3]; the member's labels at the changed rows
+ *   member_labels     : int32 [n_src][F][MHC_MAX_RANK]; the member's labels at the changed
+ *                       rows
  * "[shared rows; member rows]" is the matrix whose rows are, in order, the reference
  * tuple's labels at the positions not in fam_rows (ascending), then the member's labels
  * at fam_rows (ascending), and whose columns are the sink term's labels.

@@ -308,34 +308,12 @@ __device__ __forceinline__ void two_cof(int n_rt, const cd* __restrict__ Binv, c
   }
 }
 
-// Compact form of two_cof for the scatter: alpha = h . y and eta = h[0..M) B^{-1} (written
-// to Mst[0] and Mst[1 + m]); the scatter forms cof[m][q] = alpha B^{-1}[q][m] - eta_m y_q
-// (q < M) and cof[m][M] = -det(B) eta_m itself, so a sink stages M + 1 values, not M n.
-template <int NC, int NFIX>
-__device__ __forceinline__ void two_eta(int n_rt, const cd* __restrict__ Binv, const cd* h,
-                                        const cd* __restrict__ Y, int ys, cd* Mst) {
-  constexpr int UNR = NFIX ? NC : 1;
-  const int n = NFIX ? NFIX : n_rt;
-  const int M = n - 1;
-  cd alpha = dev::cmul(h[0], Y[0]);
-#pragma unroll UNR
-  for (int q = 1; q < n; q++) alpha = dev::cfma(h[q], Y[q * ys], alpha);
-  Mst[0] = alpha;
-#pragma unroll UNR
-  for (int m = 0; m < M; m++) {
-    cd eta = make_double2(0.0, 0.0);
-#pragma unroll UNR
-    for (int q = 0; q < M; q++) eta = dev::cfma(h[q], __ldg(Binv + q * M + m), eta);
-    Mst[1 + m] = eta;
-  }
-}
-
 // Pass 2 of one (sink, flavour): the aggregated member row h = sum_c gamma_c g_c and the
 // shared-row cofactors of [A; h] into Mst (row-major M x n) -- from B^{-1} for a two-sided
 // block, from the recomputed shared-row LU otherwise, from signed minors where the pivot
 // guard fired.  With NFIX the row h stays in registers.
 template <int NC, int NFIX>
-__device__ __forceinline__ int cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n_rt, int W,
+__device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n_rt, int W,
                                          int mem0, int kW, double wj, int tid, int T,
                                          const int32_t* __restrict__ col, const int32_t* __restrict__ arow,
                                          const cd* Dets, const cd* Y, bool guarded, const cd* Binv,
@@ -354,19 +332,21 @@ __device__ __forceinline__ int cof_pass(const FwdArgs& a, const BwdArgs& B, int 
 #pragma unroll UNR
     for (int q = 0; q < n; q++) h[q] = dev::cfma(g, dev::ldS(brow + col[q]), h[q]);
   }
-  if (!guarded && Binv) {
-    two_eta<NC, NFIX>(n, Binv, h, Y, T, Mst);
-    return 1;
-  }
   bool ok = false;
-  if (!guarded) ok = lu_block<NC, NFIX>(S, L, n, arow, col, h, Mst, a.kp);
+  if (!guarded) {
+    if (Binv) {
+      two_cof<NC, NFIX>(n, Binv, detB, h, Y, T, Mst);
+      ok = true;
+    } else {
+      ok = lu_block<NC, NFIX>(S, L, n, arow, col, h, Mst, a.kp);
+    }
+  }
   if (!ok) {
     cd hl[NC];
 #pragma unroll UNR
     for (int q = 0; q < n; q++) hl[q] = h[q];
     minors_block<NC>(S, L, n, arow, col, hl, const_cast<cd*>(Y), T, Mst);
   }
-  return 0;
 }
 
 // Family of rank k (k = 2, 3 changed rows), shared rows A ((n-k) x n), member rows
@@ -390,7 +370,7 @@ __device__ __forceinline__ void adjugate(const cd (&D)[RK][RK], cd (&adj)[RK][RK
     adj[1][0] = dev::cneg(D[1][0]);
     adj[1][1] = D[0][0];
     *det = dev::cfms(D[0][1], D[1][0], dev::cmul(D[0][0], D[1][1]));
-  } else {
+  } else if constexpr (RK == 3) {
     // adj[j][i] = (-1)^(i+j) minor(i, j)
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -402,6 +382,25 @@ __device__ __forceinline__ void adjugate(const cd (&D)[RK][RK], cd (&adj)[RK][RK
         adj[j][i] = ((i + j) & 1) ? dev::cneg(m) : m;
       }
     *det = dev::cfma(D[0][2], adj[2][0], dev::cfma(D[0][1], adj[1][0], dev::cmul(D[0][0], adj[0][0])));
+  } else {
+    // RK >= 4: adj[j][i] = (-1)^(i+j) det(D without row i and column j), each by a small LU
+    // (no division by det D, so a singular D is exact); det D along the first row
+#pragma unroll
+    for (int i = 0; i < RK; i++)
+#pragma unroll
+      for (int j = 0; j < RK; j++) {
+        cd mn[RK - 1][RK - 1];
+#pragma unroll
+        for (int r = 0; r < RK - 1; r++)
+#pragma unroll
+          for (int c = 0; c < RK - 1; c++) mn[r][c] = D[r < i ? r : r + 1][c < j ? c : c + 1];
+        const cd m = dev::small_det<RK - 1>(mn);
+        adj[j][i] = ((i + j) & 1) ? dev::cneg(m) : m;
+      }
+    cd d = dev::cmul(D[0][0], adj[0][0]);
+#pragma unroll
+    for (int j = 1; j < RK; j++) d = dev::cfma(D[0][j], adj[j][0], d);
+    *det = d;
   }
 }
 
@@ -813,8 +812,26 @@ __device__ __noinline__ void scatter_rowsk(const FwdArgs& a, const BwdArgs& B, i
   }
 }
 
+// One (sink, flavour) block of a family of rank RK >= 2: the cofactor pass (redone with
+// complete pivoting or signed minors where the shared rows fail the pivot guard) and the
+// warp's scatter.  Called by the whole warp.
+template <int NCMAX, int RK>
+__device__ __forceinline__ void rank_block(const FwdArgs& a, const BwdArgs& B, int f, int n, int mem0, int kW,
+                                           int tid, int T, int warp, int lane, int nlive,
+                                           const int32_t* col, const int32_t* arow, const cd* Dets,
+                                           const cd* Ysm, bool gd, cd* myStage, const cd* Stage, cd* Rk,
+                                           int myQ, int mynsh, cd* Df) {
+  const cd* Yf = Ysm + (size_t)a.yoff[f] * T + tid;
+  if (!cof_passk<NCMAX, RK>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk))
+    cof_passk_guarded<NCMAX, RK>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, const_cast<cd*>(Yf), myStage,
+                                 Rk);
+  __syncwarp();
+  scatter_rowsk<NCMAX, RK>(a, B, f, n, kW, nlive, T, warp, lane, col, myQ, mynsh, Stage, Ysm, Rk, Df);
+  __syncwarp();
+}
+
 template <int NCMAX>
-__device__ __forceinline__ int dispatch_cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n, int W,
+__device__ __forceinline__ void dispatch_cof_pass(const FwdArgs& a, const BwdArgs& B, int f, int n, int W,
                                                   int mem0, int kW, double wj, int tid, int T,
                                                   const int32_t* col, const int32_t* arow, const cd* Dets,
                                                   const cd* Y, bool guarded, const cd* Binv, cd detB,
@@ -822,14 +839,14 @@ __device__ __forceinline__ int dispatch_cof_pass(const FwdArgs& a, const BwdArgs
 #define MHC_COF(NN) cof_pass<NN, NN>(a, B, f, NN, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, \
                                      Binv, detB, Mst)
   switch (n) {
-    case 1: return MHC_COF(1);
-    case 2: return MHC_COF(2);
-    case 3: return MHC_COF(3);
-    case 4: return MHC_COF(4);
-    case 5: return MHC_COF(5);
-    case 6: return MHC_COF(6);
+    case 1: MHC_COF(1); return;
+    case 2: MHC_COF(2); return;
+    case 3: MHC_COF(3); return;
+    case 4: MHC_COF(4); return;
+    case 5: MHC_COF(5); return;
+    case 6: MHC_COF(6); return;
     default:
-      return cof_pass<NCMAX, 0>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, Binv, detB, Mst);
+      cof_pass<NCMAX, 0>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets, Y, guarded, Binv, detB, Mst);
   }
 #undef MHC_COF
 }
@@ -852,7 +869,7 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
                                              int kW, int mem0, int nlive, int T, int warp, int lane,
                                              const int32_t* __restrict__ mycol, int myQ, int mynsh,
                                              const cd* Stage, const cd* Ysm,
-                                             const cd* Dets, cd* Df, int W, int mymode) {
+                                             const cd* Dets, cd* Df) {
   constexpr int UNR = NFIX ? NC : 1;
   constexpr unsigned FULL = 0xffffffffu;
   const int n = NFIX ? NFIX : n_rt;
@@ -891,7 +908,6 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
         const int Qj = __shfl_sync(FULL, myQ, src);
         const int nsj = __shfl_sync(FULL, mynsh, src);
         const int rep = __shfl_sync(FULL, myrep, src);
-        const int modej = __shfl_sync(FULL, mymode, src);
         int lab = 0;  // the label of this cell's column in sink jl
 #pragma unroll UNR
         for (int p = 0; p < n; p++) {
@@ -916,24 +932,7 @@ __device__ __forceinline__ void scatter_rows(const FwdArgs& a, const BwdArgs& B,
         }
         const int ts = warp * 32 + jl;
         const cd g = (mem && !decltype(sh)::value) ? Dets[dix(c, f, B.kmax, T, ts)] : make_double2(1.0, 0.0);
-        cd v;
-        if (mem) {
-          v = Ycol[ts];
-        } else if (modej) {
-          // compact staging of a two-sided block: alpha B^{-1}[q][s] - eta_s y_q, or
-          // -det(B) eta_s for the changed column
-          const cd* st = Stage + (size_t)ts * B.mn_max;
-          const int64_t wq = (int64_t)W * a.n_q + Qj;
-          const cd eta = st[1 + s];
-          if (q < M) {
-            const cd bi = __ldg(B.kinv + wq * B.kistride + B.kioff[f] + q * M + s);
-            v = dev::cfms(eta, Ycol[ts], dev::cmul(st[0], bi));
-          } else {
-            v = dev::cneg(dev::cmul(__ldg(a.kbuf + wq * a.kstride + a.koff[f] + M * M + M + 1), eta));
-          }
-        } else {
-          v = Stage[(size_t)ts * B.mn_max + s * n + q];
-        }
+        const cd v = mem ? Ycol[ts] : Stage[(size_t)ts * B.mn_max + s * n + q];
         const bool shcol = q < nsh;
         if (!rep) {
           // one complex FMA (an addition in a step of shared rows) per lane, on the register
@@ -969,10 +968,9 @@ template <int NCMAX>
 __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs& B, int f, int n,
                                                  int kW, int mem0, int nlive, int T, int warp, int lane,
                                                  const int32_t* mycol, int myQ, int mynsh,
-                                                 const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df,
-                                                 int W, int mymode) {
+                                                 const cd* Stage, const cd* Ysm, const cd* Dets, cd* Df) {
 #define MHC_SC(NN) scatter_rows<NN, NN>(a, B, f, NN, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, \
-                                        Stage, Ysm, Dets, Df, W, mymode)
+                                        Stage, Ysm, Dets, Df)
   switch (n) {
     case 1: MHC_SC(1); return;
     case 2: MHC_SC(2); return;
@@ -982,7 +980,7 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
     case 6: MHC_SC(6); return;
     default:
       scatter_rows<NCMAX, 0>(a, B, f, n, kW, mem0, nlive, T, warp, lane, mycol, myQ, mynsh, Stage, Ysm,
-                             Dets, Df, W, mymode);
+                             Dets, Df);
   }
 #undef MHC_SC
 }
@@ -1112,34 +1110,30 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
       if constexpr (NCMAX >= 10) {
         const int rho = a.fam_rank[(int64_t)W * a.F + f];
-        if (rho >= 2) {  // two or three changed rows
+        if (rho >= 2) {  // rank-k families (k = 2 .. MHC_MAX_RANK; rank k needs n_f >= 4k + 2)
           cd* Rk = B.r2 + (size_t)cta * B.kmax * B.rk2 * T;
-          const cd* Yf = Ysm + (size_t)a.yoff[f] * T + tid;
           const bool gd = (pguard >> f) & 1;
-          // a shared-row factorisation that fails the pivot guard is redone with complete
-          // pivoting (or signed minors for exactly dependent shared rows)
-          if (rho == 2) {
-            if (!cof_passk<NCMAX, 2>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk))
-              cof_passk_guarded<NCMAX, 2>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets,
-                                          const_cast<cd*>(Yf), myStage, Rk);
-          } else if constexpr (NCMAX >= 14) {
-            if (!cof_passk<NCMAX, 3>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets, Yf, gd, myStage, Rk))
-              cof_passk_guarded<NCMAX, 3>(a, f, n, mem0, kW, tid, T, B.kmax, col, arow, Dets,
-                                          const_cast<cd*>(Yf), myStage, Rk);
-          }
-          __syncwarp();
           const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
           const int nlive = rem < 32 ? (int)rem : 32;
           const int mynsh = qtwo ? n - a.q_rank[(int64_t)Q * a.F + f] : 0;
           cd* Df = Dw + (size_t)f * B.slots_max * B.Lmax;
+#define MHC_RB(K) rank_block<NCMAX, K>(a, B, f, n, mem0, kW, tid, T, warp, lane, nlive, col, arow, Dets, Ysm, gd, \
+                                       myStage, Stage, Rk, qtwo ? Q : -1, mynsh, Df)
           if (rho == 2) {
-            scatter_rowsk<NCMAX, 2>(a, B, f, n, kW, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh, Stage, Ysm,
-                                    Rk, Df);
+            MHC_RB(2);
           } else if constexpr (NCMAX >= 14) {
-            scatter_rowsk<NCMAX, 3>(a, B, f, n, kW, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh, Stage, Ysm,
-                                    Rk, Df);
+            if (rho == 3) {
+              MHC_RB(3);
+            } else if constexpr (NCMAX >= 18) {
+              if (rho == 4) {
+                MHC_RB(4);
+              } else if constexpr (NCMAX >= 32) {
+                if (rho == 5) MHC_RB(5);
+                if (rho == 6) MHC_RB(6);
+              }
+            }
           }
-          __syncwarp();
+#undef MHC_RB
           continue;
         }
       }
@@ -1149,7 +1143,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       // B^{-1} shared by the (family, sink family) block
       const cd* Binv = twoc ? B.kinv + wq * B.kistride + B.kioff[f] : nullptr;
       const cd detB = twoc ? a.kbuf[wq * a.kstride + a.koff[f] + M * M + M + 1] : make_double2(0.0, 0.0);
-      const int mymode = dispatch_cof_pass<NCMAX>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets,
+      dispatch_cof_pass<NCMAX>(a, B, f, n, W, mem0, kW, wj, tid, T, col, arow, Dets,
                                Ysm + (size_t)a.yoff[f] * T + tid, (pguard >> f) & 1, Binv, detB, myStage);
       __syncwarp();
 
@@ -1159,7 +1153,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int64_t rem = a.n_snk - ((int64_t)tile * T + warp * 32);
       const int nlive = rem < 32 ? (int)rem : 32;
       dispatch_scatter<NCMAX>(a, B, f, n, kW, mem0, nlive, T, warp, lane, col, qtwo ? Q : -1, mynsh,
-                              Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax, W, mymode);
+                              Stage, Ysm, Dets, Dw + (size_t)f * B.slots_max * B.Lmax);
       __syncwarp();
     }
   }

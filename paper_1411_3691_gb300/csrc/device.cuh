@@ -179,7 +179,47 @@ __device__ __forceinline__ bool shared_rows(const cd* __restrict__ S, int L, int
   return M > 0 && (zero || emax - emin > kp);
 }
 
-// det of member rows B against the cached solve: RHO = 1: b . y; RHO = 2: sd det(B Z).
+// Determinant of a K x K matrix in registers by LU with partial pivoting (largest
+// |re| + |im|, the first such row on ties); an exactly zero pivot column gives 0.  D is
+// destroyed.  Used for the K x K block B Z of a rank-K family (K >= 4).
+template <int K>
+__device__ __forceinline__ cd small_det(cd (&D)[K][K]) {
+  cd det = make_double2(1.0, 0.0);
+  int parity = 0;
+  bool zero = false;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    double best = abs1(D[k][k]);
+#pragma unroll
+    for (int i = k + 1; i < K; i++) {
+      const double m = abs1(D[i][k]);
+      const bool sw = gt_nonneg(m, best);
+      best = sw ? m : best;
+      parity ^= (int)sw;
+#pragma unroll
+      for (int q = k; q < K; q++) {
+        const cd t = D[k][q];
+        D[k][q] = sw ? D[i][q] : t;
+        D[i][q] = sw ? t : D[i][q];
+      }
+    }
+    zero |= __double_as_longlong(best) == 0;
+    det = k == 0 ? D[k][k] : cmul(det, D[k][k]);
+    if (k + 1 < K) {
+      const cd rc = crcp(D[k][k]);
+#pragma unroll
+      for (int i = k + 1; i < K; i++) {
+        const cd l = cmul(D[i][k], rc);
+#pragma unroll
+        for (int q = k + 1; q < K; q++) D[i][q] = cfms(l, D[k][q], D[i][q]);
+      }
+    }
+  }
+  if (zero) return make_double2(0.0, 0.0);
+  return parity ? cneg(det) : det;
+}
+
+// det of member rows B against the cached solve: RHO = 1: b . y; RHO >= 2: sd det(B Z).
 // *fail is set when |det| < 2^-kc |b| |y| (the normalised lemma factor, by exponents).
 template <int NC, int NFIX, int RHO>
 __device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_rt,
@@ -229,6 +269,31 @@ __device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_
     const cd m2 = cfms(D[1][1], D[2][0], cmul(D[1][0], D[2][1]));
     const cd dd = cfma(D[0][2], m2, cfms(D[0][1], m1, cmul(D[0][0], m0)));
     const cd d = cmul(Y[3 * n * ys], dd);
+    *fail = expo(d) < eb + ey - kc;
+    return d;
+  } else if (RHO >= 4) {
+    // sd det(B Z), B the RHO member rows: RHO x RHO dots, then a small LU
+    cd D[RHO][RHO];
+    int eb = 0;
+#pragma unroll
+    for (int u = 0; u < RHO; u++)
+#pragma unroll
+      for (int v = 0; v < RHO; v++) D[u][v] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < RHO; u++) {
+      const cd* ru = S + (size_t)lab[u] * L;
+      int e = -4096;
+#pragma unroll UNR
+      for (int q = 0; q < n; q++) {
+        const cd b = ldS(ru + colp[q]);
+        e = max(e, expo(b));
+#pragma unroll
+        for (int v = 0; v < RHO; v++) D[u][v] = cfma(b, Y[(v * n + q) * ys], D[u][v]);
+      }
+      eb += e;
+    }
+    const cd dd = small_det<RHO>(D);
+    const cd d = cmul(Y[RHO * n * ys], dd);
     *fail = expo(d) < eb + ey - kc;
     return d;
   } else {

@@ -87,6 +87,13 @@ __device__ __forceinline__ bool dispatch_shared(int n, int rho, const cd* S, int
   if constexpr (NCMAX >= 14) {  // three changed rows (n_f >= 14 only)
     if (rho == 3) return shared_rows<NCMAX, 0, 3>(S, L, n, arow, col, Y, ys, ey, kp);
   }
+  if constexpr (NCMAX >= 18) {  // rank k for n_f >= 4k + 2: 4 from n_f = 18
+    if (rho == 4) return shared_rows<NCMAX, 0, 4>(S, L, n, arow, col, Y, ys, ey, kp);
+  }
+  if constexpr (NCMAX >= 32) {  // 5 from n_f = 22, 6 from n_f = 26
+    if (rho == 5) return shared_rows<NCMAX, 0, 5>(S, L, n, arow, col, Y, ys, ey, kp);
+    if (rho == 6) return shared_rows<NCMAX, 0, 6>(S, L, n, arow, col, Y, ys, ey, kp);
+  }
   return rho == 1 ? shared_rows<NCMAX, 0, 1>(S, L, n, arow, col, Y, ys, ey, kp)
                   : shared_rows<NCMAX, 0, 2>(S, L, n, arow, col, Y, ys, ey, kp);
 }
@@ -112,6 +119,13 @@ __device__ __forceinline__ cd dispatch_member(int n, int rho, const cd* S, int L
 #undef MHC_MD
   if constexpr (NCMAX >= 14) {  // three changed rows (n_f >= 14 only)
     if (rho == 3) return member_det<NCMAX, 0, 3>(S, L, n, lab, col, Y, ys, ey, kc, fail);
+  }
+  if constexpr (NCMAX >= 18) {
+    if (rho == 4) return member_det<NCMAX, 0, 4>(S, L, n, lab, col, Y, ys, ey, kc, fail);
+  }
+  if constexpr (NCMAX >= 32) {
+    if (rho == 5) return member_det<NCMAX, 0, 5>(S, L, n, lab, col, Y, ys, ey, kc, fail);
+    if (rho == 6) return member_det<NCMAX, 0, 6>(S, L, n, lab, col, Y, ys, ey, kc, fail);
   }
   if constexpr (NCMAX >= 18) {  // the n of the large-nucleus and batched workloads
     if (n == 9)

@@ -26,7 +26,12 @@ constexpr size_t kBucketWindow = 2048;
 // a rank-2 update (4 dot products per member over n - 2 shared rows) saves too little over
 // splitting the family.
 constexpr int kRank2MinN = 10;
-constexpr int kRank3MinN = 14;  // three changed rows only for n_f >= 14 (opts.rank3)
+// rank k (k changed rows per flavour) only for n_f >= 4k + 2: rank 2 from 10, rank 3 from 14
+int rank_min_n(int k) { return 4 * k + 2; }
+// Largest number of leave-d-out keys per build of the candidate list: above it the keys
+// leave out at most two labels (pairs that differ in more labels in the key flavour are
+// then not adjacent in the graph).
+constexpr double kMaxKeys = 5e7;
 
 uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
@@ -123,6 +128,7 @@ double flops_shared_rows(int n, int rho) {
 double flops_member(int n, int rho) {
   if (n <= 0) return 0.0;
   const double dot = 6.0 + 8.0 * (n - 1);
+  if (rho >= 4) return rho * rho * dot + flops_fresh_lu(rho) + 6.0;  // k x k LU det, times sd
   if (rho == 3) return 9.0 * dot + 3.0 * 14.0 + 22.0 + 6.0;  // 3x3 det by cofactors, times sd
   return rho == 2 ? 4.0 * dot + 2.0 * 6.0 + 2.0 : dot;
 }
@@ -223,25 +229,47 @@ std::vector<std::vector<int32_t>> dominated_sets(const std::vector<int32_t>& lab
   // ---- candidate pairs: shared leave-d-out keys of the key flavour ------------------
   std::vector<std::pair<uint64_t, int32_t>> keys;
   if (f0 >= 0) {
-    const int n = n_f[f0], d = std::min(dmax[f0], n);
-    keys.reserve((size_t)N * (d == 1 ? n : n * (n - 1) / 2 + 1));
-    std::vector<int32_t> rest;
+    const int n = n_f[f0];
+    int d = std::min(dmax[f0], n);
+    auto choose = [](int a, int b) {
+      double c = 1.0;
+      for (int t = 0; t < b; t++) c = c * (a - t) / (t + 1);
+      return c;
+    };
+    while (d > 2 && (double)N * choose(n, d) > kMaxKeys) d--;
+    keys.reserve((size_t)((double)N * (d == 1 ? n : choose(n, d))));
+    std::vector<int> skip(d);
     for (int64_t i = 0; i < N; i++) {
       const int32_t* s = &sorted[i * Tn + off_f[f0]];
-      auto emit = [&](int skip1, int skip2) {
+      // one key per d-subset of positions left out: the hash of the remaining labels
+      auto emit = [&]() {
         uint64_t h = 0x9e3779b97f4a7c15ULL;
-        for (int m = 0; m < n; m++)
-          if (m != skip1 && m != skip2) h = mix64(h ^ (uint64_t)(uint32_t)s[m]);
+        int t = 0;
+        for (int m = 0; m < n; m++) {
+          if (t < d && skip[t] == m) {
+            t++;
+            continue;
+          }
+          h = mix64(h ^ (uint64_t)(uint32_t)s[m]);
+        }
         keys.emplace_back(h, (int32_t)i);
       };
       if (d == 1) {
         for (int m = 0; m < n; m++)
-          if (m == 0 || s[m] != s[m - 1]) emit(m, -1);
-      } else if (n == 2) {
-        emit(0, 1);
+          if (m == 0 || s[m] != s[m - 1]) {
+            skip[0] = m;
+            emit();
+          }
       } else {
-        for (int m1 = 0; m1 < n; m1++)
-          for (int m2 = m1 + 1; m2 < n; m2++) emit(m1, m2);
+        for (int t = 0; t < d; t++) skip[t] = t;
+        for (;;) {  // every d-subset of [0, n) in lexicographic order
+          emit();
+          int t = d - 1;
+          while (t >= 0 && skip[t] == n - d + t) t--;
+          if (t < 0) break;
+          skip[t]++;
+          for (int u = t + 1; u < d; u++) skip[u] = skip[u - 1] + 1;
+        }
       }
     }
   } else {
@@ -326,11 +354,14 @@ mhc_status build_plan(Plan& p) {
   const int rank2 = p.opts.rank2 ? 1 : 0;
   const int kmax = p.opts.max_family;
 
-  // changed labels allowed per flavour: sources up to 3 (opts.rank3), sinks up to 2
+  // changed labels allowed per flavour: sources up to the largest rank the options allow
+  // for n_f (opts.max_rank, or 3 with opts.rank3, else 2), sinks up to 2
+  const int rmax = !rank2 ? 1 : (p.opts.max_rank > 0 ? p.opts.max_rank : (p.opts.rank3 ? 3 : 2));
   std::vector<int> dmax(F), dmax_snk(F);
   for (int f = 0; f < F; f++) {
-    dmax[f] = (rank2 && p.n_f[f] >= kRank2MinN) ? 2 : 1;
-    if (rank2 && p.opts.rank3 && p.n_f[f] >= kRank3MinN) dmax[f] = 3;
+    dmax[f] = 1;
+    for (int k = 2; k <= rmax; k++)
+      if (p.n_f[f] >= rank_min_n(k)) dmax[f] = k;
     dmax_snk[f] = std::min(dmax[f], 2);
   }
   int64_t edges = 0;
@@ -349,7 +380,7 @@ mhc_status build_plan(Plan& p) {
   p.mem_lab.clear();
   p.src_member.assign(N, -1);
   p.mem_family.clear();
-  int64_t rank2_blocks = 0, rank3_blocks = 0;
+  int64_t rank2_blocks = 0, rank3_blocks = 0, rank4p_blocks = 0;
   p.max_members = 0;
 
   struct Member {
@@ -414,6 +445,7 @@ mhc_status build_plan(Plan& p) {
         ranks[f] = (int32_t)R.size();
         if (R.size() == 2) rank2_blocks++;
         if (R.size() == 3) rank3_blocks++;
+        if (R.size() >= 4) rank4p_blocks++;
         for (size_t k = 0; k < R.size(); k++) rows[MHC_MAX_RANK * f + k] = R[k];
         // [shared rows ascending; changed rows ascending] and the sign of that reordering
         std::vector<int> order;
@@ -554,6 +586,7 @@ mhc_status build_plan(Plan& p) {
   s.families = p.n_fam;
   s.rank2_family_flavours = rank2_blocks;
   s.rank3_family_flavours = rank3_blocks;
+  s.rank4plus_family_flavours = rank4p_blocks;
   s.members = (int64_t)p.mem_term.size();
   s.graph_edges = edges;
   s.sink_families = p.n_qfam;
@@ -624,7 +657,9 @@ mhc_status build_plan(Plan& p) {
         // rows' coefficients; per sink the LU of A1 ((n-k) x (n-k)), the columns of A1^{-1},
         // the shared block rows; the scatter of k per member rows and n-k shared rows
         const double K = rk, Mk = n - rk;
-        const double adj = rk == 2 ? 6.0 + 8.0 : 9.0 * 14.0 + 22.0;
+        const double adj = rk == 2 ? 6.0 + 8.0
+                           : rk == 3 ? 9.0 * 14.0 + 22.0
+                                     : K * K * flops_fresh_lu(rk - 1) + 8.0 * K;  // minors by small LUs
         double rr = k * (2.0 * K * K * 8.0 * n + adj + 8.0 + 2.0 * K * K * 6.0);
         rr += flops_adjugate((int)Mk);
         for (int i = 0; i < (int)Mk; i++)
@@ -766,6 +801,11 @@ mhc_status mhc_plan(mhc_plan_t* out, int32_t F, const int32_t* n_f, const int32_
     if (!(p->opts.tau_parent >= 0.0 && p->opts.tau_parent < 1.0) ||
         !(p->opts.tau_child >= 0.0 && p->opts.tau_child < 1.0)) {
       set_error("mhc_plan: tau_parent and tau_child must be in [0, 1)");
+      delete p;
+      return MHC_EINVAL;
+    }
+    if (p->opts.max_rank < 0 || p->opts.max_rank > MHC_MAX_RANK) {
+      set_error("mhc_plan: max_rank must be in [0, MHC_MAX_RANK]");
       delete p;
       return MHC_EINVAL;
     }

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libmhc.so")
 
 MHC_OK, MHC_EINVAL, MHC_ENOMEM, MHC_ECUDA, MHC_ETIMEOUT, MHC_ENONFINITE, MHC_EUNSUPPORTED = range(7)
-MHC_MAX_RANK = 3  # stride of the changed-row tables (include/mhc.h)
+MHC_MAX_RANK = 6  # stride of the changed-row tables (include/mhc.h)
 STATUS_NAMES = ["MHC_OK", "MHC_EINVAL", "MHC_ENOMEM", "MHC_ECUDA", "MHC_ETIMEOUT",
                 "MHC_ENONFINITE", "MHC_EUNSUPPORTED"]
 MHC_NMAX = 32
@@ -45,7 +45,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("tau_parent", ctypes.c_double), ("tau_child", ctypes.c_double),
                 ("sink_tile", ctypes.c_int32), ("rank2", ctypes.c_int32),
                 ("max_family", ctypes.c_int32), ("one_sided", ctypes.c_int32),
-                ("rank3", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("rank3", ctypes.c_int32), ("max_rank", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
                 ("refactor_child", ctypes.c_int64), ("sink_families", ctypes.c_int64),
                 ("two_sided_blocks", ctypes.c_int64), ("backward_flops_per_call", ctypes.c_double),
                 ("rank3_family_flavours", ctypes.c_int64), ("refactor_flops", ctypes.c_double),
-                ("reserved", ctypes.c_int64 * 1)]
+                ("rank4plus_family_flavours", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -74,8 +74,11 @@ def add_twins(rng, S: np.ndarray, n_twins: int = 8, noise: float = 1e-13):
 
 
 def make_side(rng, n_f, L_f, family_sizes, two_row_frac=0.0, forced_frac=0.0,
-              n_ordinary=None, twin_origin=None, three_row_frac=0.0):
-    """Term list of one side; returns (labels int32 [N, sum n_f], info dict)."""
+              n_ordinary=None, twin_origin=None, three_row_frac=0.0, more_rows=None):
+    """Term list of one side; returns (labels int32 [N, sum n_f], info dict).  more_rows:
+    {k: fraction} (every flavour) or a list of such dicts (one per flavour) for families
+    whose members change k >= 4 rows of a flavour (drawn only when given, so the other
+    workloads keep their random streams)."""
     F = len(n_f)
     Tn = int(sum(n_f))
     N = int(sum(family_sizes))
@@ -97,7 +100,14 @@ def make_side(rng, n_f, L_f, family_sizes, two_row_frac=0.0, forced_frac=0.0,
             parent = np.sort(rng.choice(ordinary, size=n, replace=False)).astype(np.int32)
             two = n >= 2 and rng.random() < two_row_frac
             three = three_row_frac > 0 and n >= 3 and rng.random() < three_row_frac
-            if three:
+            big = 0
+            mr = more_rows[f] if isinstance(more_rows, (list, tuple)) else more_rows
+            for k in sorted(mr or {}):
+                if n >= k and rng.random() < mr[k]:
+                    big = k
+            if big:
+                rr = tuple(sorted(int(x) for x in rng.choice(n, size=big, replace=False)))
+            elif three:
                 rr = tuple(sorted(int(x) for x in rng.choice(n, size=3, replace=False)))
             elif two:
                 rr = tuple(sorted(int(x) for x in rng.choice(n, size=2, replace=False)))
@@ -137,7 +147,7 @@ def make_side(rng, n_f, L_f, family_sizes, two_row_frac=0.0, forced_frac=0.0,
 
 
 def make_workload(name, n_f, L_f, fam_src, fam_snk, diag=2.0, seed=0, two_row_frac=0.0,
-                  forced_frac=0.0, twins=0, three_row_frac=0.0):
+                  forced_frac=0.0, twins=0, three_row_frac=0.0, more_rows=None):
     ss = np.random.SeedSequence(seed)
     r_S, r_src, r_snk, _ = [np.random.default_rng(s) for s in ss.spawn(4)]
     S = [make_S(r_S, int(L), diag) for L in L_f]
@@ -147,7 +157,7 @@ def make_workload(name, n_f, L_f, fam_src, fam_snk, diag=2.0, seed=0, two_row_fr
         twin_origin = [add_twins(r_S, s, twins) for s in S]
         n_ord = [int(L) - twins for L in L_f]
     ls, info_s = make_side(r_src, n_f, L_f, fam_src, two_row_frac, forced_frac, n_ord, twin_origin,
-                           three_row_frac)
+                           three_row_frac, more_rows)
     lk, info_k = make_side(r_snk, n_f, L_f, fam_snk, two_row_frac, 0.0, n_ord, twin_origin, three_row_frac)
     ws = r_src.normal(size=ls.shape[0])
     wk = r_snk.normal(size=lk.shape[0])

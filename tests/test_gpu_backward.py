@@ -306,3 +306,24 @@ def test_three_row_families(M):
         assert plan.stats()["rank3_family_flavours"] > 0
         plan.close()
         check_vs_oracle(M, w, opts)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_rank_k_families(M, k):
+    """The adjoint of rank-k families (k = 4, 5: member-row cofactors sd Z adj(D), the
+    shared rows' from the right inverse of the shared rows; adj(D) from (k-1) x (k-1)
+    minors) against the oracle's Jacobi gradient, with and without sink families."""
+    if k == 4:
+        w = wl.make_workload("r4", [18, 12], [96, 60], [5, 4, 3, 4], [4, 3, 5], diag=3.0, seed=95,
+                             two_row_frac=0.3, more_rows=[{4: 0.7}, {}])
+    else:
+        w = wl.make_workload("r5", [22, 10], [110, 40], [5, 4, 3], [3, 4, 2], diag=3.0, seed=96,
+                             more_rows=[{4: 0.3, 5: 0.6}, {}])
+    for one_sided in (0, 1):
+        opts = M.default_opts()
+        opts.max_rank = k
+        opts.one_sided = one_sided
+        plan = M.Plan.from_workload(w, opts)
+        assert int(plan.families()["rank"].max()) == k
+        plan.close()
+        check_vs_oracle(M, w, opts)

@@ -282,3 +282,34 @@ def test_forced_members_against_two_column_sink_families(M):
     fresh18 = 18 * 19 / 2 + 6 * 17 + 3 * 18 * 17 + 8 * 17 * 18 * 35 / 6 + 6 * 17
     assert 0 < st["refactor_flops"] < 0.5 * n_ref * fresh18
     plan.close()
+
+
+def _rank_k_workload(k):
+    """Source families that change k rows of their first flavour (rank k needs n_f >= 4k + 2:
+    n_f = 18 for k = 4, 22 for k = 5), two-row families in the other flavour."""
+    if k == 4:
+        return wl.make_workload("r4", [18, 12], [96, 60], [5, 4, 4, 3, 6], [5, 6, 4, 20], diag=3.0, seed=93,
+                                two_row_frac=0.3, more_rows=[{4: 0.7}, {}])
+    return wl.make_workload("r5", [22, 10], [110, 40], [5, 4, 3, 6], [4, 5, 3, 12], diag=3.0, seed=94,
+                            more_rows=[{4: 0.3, 5: 0.6}, {}])
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("one_sided", [0, 1])
+def test_rank_k_families(M, k, one_sided):
+    """The general rank-k update (k null vectors of the shared rows, a k x k determinant per
+    member by a small LU), k = 4 and 5: C against the oracle with and without sink families,
+    and every pair's determinants through the probe."""
+    w = _rank_k_workload(k)
+    opts = M.default_opts()
+    opts.max_rank = k
+    opts.one_sided = one_sided
+    C, plan, S = gpu_C(M, w, opts)
+    assert plan.stats()["rank4plus_family_flavours"] > 0
+    assert int(plan.families()["rank"].max()) == k
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
+    ii, jj = np.meshgrid(np.arange(len(w.w_src)), np.arange(len(w.w_snk)), indexing="ij")
+    check_pairs(M, w, plan, S, ii.ravel(), jj.ravel())
+    plan.close()

@@ -59,6 +59,10 @@ def test_null_arguments_are_rejected(M):
         assert L.mhc_last_error(), name
 
 
+def fam_max_rank(plan):
+    return int(plan.families()["rank"].max())
+
+
 def _walk(M, w, plan):
     """Evaluate every (member, sink) determinant from the plan's families: the shared rows
     of the reference tuple plus the member's rows (LAPACK det), times the member sign."""
@@ -87,7 +91,8 @@ def _walk(M, w, plan):
     return dets
 
 
-@pytest.mark.parametrize("name", ["deuteron", "helium4", "large", "mixed", "three_rows"])
+@pytest.mark.parametrize("name", ["deuteron", "helium4", "large", "mixed", "three_rows", "four_rows",
+                                  "five_rows"])
 def test_plan_walk_matches_oracle(M, name):
     if name == "deuteron":
         w = wl.deuteron(scale=6 / 64)
@@ -100,14 +105,24 @@ def test_plan_walk_matches_oracle(M, name):
                              two_row_frac=0.5, forced_frac=0.2, twins=8)
     elif name == "mixed":
         w = wl.make_workload("mixed", [3, 0, 7], [24, 5, 30], [5, 1, 3, 8], [3, 3], seed=9, two_row_frac=0.3)
+    elif name == "four_rows":
+        w = wl.make_workload("r4", [18, 12], [96, 60], [5, 4, 4, 3], [4, 3], diag=3.0, seed=91,
+                             two_row_frac=0.3, more_rows=[{4: 0.6}, {}])
+    elif name == "five_rows":
+        w = wl.make_workload("r5", [22, 10], [110, 40], [5, 4, 3], [3, 2], diag=3.0, seed=92,
+                             more_rows=[{4: 0.3, 5: 0.6}, {}])
     else:
         w = wl.make_workload("r3", [14, 10], [56, 40], [6, 5, 4], [4, 3], seed=61, two_row_frac=0.3,
                              three_row_frac=0.6)
     opts = M.default_opts()
     opts.rank3 = 1 if name == "three_rows" else 0
+    opts.max_rank = {"four_rows": 4, "five_rows": 5}.get(name, 0)
     plan = M.Plan.from_workload(w, opts)
     if name == "three_rows":
         assert plan.stats()["rank3_family_flavours"] > 0
+    if name in ("four_rows", "five_rows"):
+        assert plan.stats()["rank4plus_family_flavours"] > 0
+        assert fam_max_rank(plan) == opts.max_rank
     fam = plan.families()
     # every source term is a member exactly once
     assert sorted(fam["term"].tolist()) == list(range(plan.n_src))
