@@ -378,6 +378,7 @@ def run_gpu(args):
             "he4": time_config(mhc, workload(0, "he4"), flush, stream, peak, steps=20),
             "batch": time_batch(mhc, flush, stream, peak),
             "adjoint_he4": time_adjoint(mhc, workload(0, "he4"), flush, stream, peak),
+            "mixed_rows": time_grouping(mhc, flush, stream, peak),
         }
 
     if rank == 0:
@@ -431,10 +432,10 @@ def time_one_sided(mhc, w, S, out, flush, stream, two_ms, peak):
             "two_sided_speedup": ms / two_ms}
 
 
-def time_config(mhc, w, flush, stream, peak, steps=20):
+def time_config(mhc, w, flush, stream, peak, steps=20, opts=None):
     """Forward of another workload: CUDA-event time per call and fraction of the FP64 peak."""
     import torch
-    plan = mhc.Plan.from_workload(w)
+    plan = mhc.Plan.from_workload(w, opts)
     S = [torch.from_numpy(s).cuda() for s in w.S]
     out = torch.empty(2, dtype=torch.float64, device="cuda")
     ms = time_forward(plan, S, out, flush, stream, steps=steps)
@@ -445,6 +446,22 @@ def time_config(mhc, w, flush, stream, peak, steps=20):
            "flops_per_step": flops, "gpu_launches_per_step": forward_launches(plan, w, st)}
     plan.close()
     return res
+
+
+def time_grouping(mhc, flush, stream, peak):
+    """Families whose members change rows of their own (2 flavours, n_f = 12, L = 60, 4096 x
+    4096 terms, source families of 32): the work families split by the plan's flop count
+    (the default) against first fit, both timed."""
+    from paper_1411_3691_gb300 import workloads as wl
+    w = wl.make_workload("mixed_rows_n12_L60_4096x4096", [12, 12], [60, 60], [32] * 128, [16] * 256, seed=7,
+                         mixed_rows=True)
+    ff = mhc.default_opts()
+    ff.first_fit = 1
+    cost = time_config(mhc, w, flush, stream, peak)
+    first = time_config(mhc, w, flush, stream, peak, opts=ff)
+    return {"cost_grouping": cost, "first_fit": first,
+            "flops_ratio": cost["flops_per_step"] / first["flops_per_step"],
+            "speedup": first["ms_per_step"] / cost["ms_per_step"]}
 
 
 def time_adjoint(mhc, w, flush, stream, peak, steps=10):

@@ -89,7 +89,15 @@ typedef struct {
                           flavour with n_f >= 4k + 2 (rank 2: n_f >= 10, rank 3:
                           n_f >= 14, rank 4: 18, 5: 22, 6: 26).  0: 3 with rank3,
                           else 2.                                               0     */
-  int32_t reserved[5];
+  int32_t first_fit;   /* how a dominated set (Sec. 3) is split into work families whose
+                          members differ from the dominator in the same rows:
+                          0: by cost -- members with the same changed rows form
+                          groups, and the pair of groups whose merge (one shared
+                          factorisation per sink, possibly a higher rank for all
+                          members) most lowers the plan's flop count is merged
+                          until no merge lowers it; 1: first fit in term order
+                          (each member joins the first family it fits).        0     */
+  int32_t reserved[4];
 } mhc_plan_opts;
 
 /* Planner and run statistics. */

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <set>
 #include <string>
@@ -368,124 +369,6 @@ mhc_status build_plan(Plan& p) {
   std::vector<std::vector<int32_t>> dom_sets =
       dominated_sets(p.labels_src, N, F, p.n_f, p.off_f, Tn, dmax, &edges);
 
-  // ---- work families: align members, group by compatible changed rows ---------------
-  p.fam_off.assign(1, 0);
-  p.fam_rank.clear();
-  p.fam_rows.clear();
-  p.fam_ref.clear();
-  p.fam_arow.clear();
-  p.mem_term.clear();
-  p.mem_sign.clear();
-  p.mem_par.clear();
-  p.mem_lab.clear();
-  p.src_member.assign(N, -1);
-  p.mem_family.clear();
-  int64_t rank2_blocks = 0, rank3_blocks = 0, rank4p_blocks = 0;
-  p.max_members = 0;
-
-  struct Member {
-    int32_t term;
-    std::vector<Align> al;  // per flavour
-  };
-  struct Group {
-    std::vector<std::vector<int>> R;  // per flavour, ascending changed rows
-    std::vector<int> members;         // indices into the member list
-  };
-  for (auto& ds : dom_sets) {
-    const int32_t v = ds[0];
-    const int32_t* ref = &p.labels_src[(int64_t)v * Tn];
-    std::vector<Member> mems;
-    for (int32_t t : ds) {
-      Member m;
-      m.term = t;
-      for (int f = 0; f < F; f++)
-        m.al.push_back(align(ref + p.off_f[f], &p.labels_src[(int64_t)t * Tn + p.off_f[f]], p.n_f[f]));
-      mems.push_back(std::move(m));
-    }
-    std::vector<Group> groups;
-    for (int mi = 0; mi < (int)mems.size(); mi++) {
-      bool placed = false;
-      for (auto& g : groups) {
-        if ((int)g.members.size() >= kmax) continue;
-        bool ok = true;
-        std::vector<std::vector<int>> U(F);
-        for (int f = 0; f < F && ok; f++) {
-          std::set<int> u(g.R[f].begin(), g.R[f].end());
-          u.insert(mems[mi].al[f].changed.begin(), mems[mi].al[f].changed.end());
-          U[f].assign(u.begin(), u.end());
-          ok = (int)U[f].size() <= dmax[f];
-        }
-        if (ok) {
-          g.R = U;
-          g.members.push_back(mi);
-          placed = true;
-          break;
-        }
-      }
-      if (!placed) {
-        Group g;
-        g.R.resize(F);
-        for (int f = 0; f < F; f++) g.R[f] = mems[mi].al[f].changed;
-        g.members.push_back(mi);
-        groups.push_back(std::move(g));
-      }
-    }
-    for (auto& g : groups) {
-      const int64_t W = p.n_fam++;
-      std::vector<int32_t> ranks(F), rows(MHC_MAX_RANK * F, -1), arow(Tn, -1);
-      std::vector<int> eps(F, 0);
-      for (int f = 0; f < F; f++) {
-        const int n = p.n_f[f];
-        std::vector<int> R = g.R[f];
-        if (n == 0) {
-          ranks[f] = 0;
-          continue;
-        }
-        if (R.empty()) R.push_back(n - 1);
-        ranks[f] = (int32_t)R.size();
-        if (R.size() == 2) rank2_blocks++;
-        if (R.size() == 3) rank3_blocks++;
-        if (R.size() >= 4) rank4p_blocks++;
-        for (size_t k = 0; k < R.size(); k++) rows[MHC_MAX_RANK * f + k] = R[k];
-        // [shared rows ascending; changed rows ascending] and the sign of that reordering
-        std::vector<int> order;
-        int a = 0;
-        for (int m = 0; m < n; m++)
-          if (std::find(R.begin(), R.end(), m) == R.end()) {
-            order.push_back(m);
-            arow[p.off_f[f] + a++] = ref[p.off_f[f] + m];
-          }
-        for (int r : R) order.push_back(r);
-        eps[f] = perm_parity(order);
-        g.R[f] = R;
-      }
-      for (int f = 0; f < F; f++) p.fam_rank.push_back(ranks[f]);
-      p.fam_rows.insert(p.fam_rows.end(), rows.begin(), rows.end());
-      p.fam_ref.insert(p.fam_ref.end(), ref, ref + Tn);
-      p.fam_arow.insert(p.fam_arow.end(), arow.begin(), arow.end());
-      for (int mi : g.members) {
-        const Member& m = mems[mi];
-        int parity = 0, bits = 0;
-        std::vector<int32_t> lab(MHC_MAX_RANK * F, -1);
-        for (int f = 0; f < F; f++) {
-          if (p.n_f[f] == 0) continue;
-          const int pf = m.al[f].parity ^ eps[f];
-          parity ^= pf;
-          bits |= pf << f;
-          for (int k = 0; k < ranks[f]; k++) lab[MHC_MAX_RANK * f + k] = m.al[f].aligned[g.R[f][k]];
-        }
-        p.mem_lab.insert(p.mem_lab.end(), lab.begin(), lab.end());
-        p.src_member[m.term] = (int32_t)p.mem_term.size();
-        p.mem_term.push_back(m.term);
-        p.mem_sign.push_back(parity ? -1 : 1);
-        p.mem_par.push_back(bits);
-        p.mem_family.push_back((int32_t)W);
-      }
-      p.fam_off.push_back((int64_t)p.mem_term.size());
-      p.max_members = std::max(p.max_members, (int)g.members.size());
-    }
-  }
-
   // ---- sink families for the two-sided update (Sec. 2: a sink term that differs in one
   // label changes one column; the same greedy dominating set on the sink side, with two
   // changed columns allowed where two changed rows are) ---------------------------------
@@ -573,6 +456,222 @@ mhc_status build_plan(Plan& p) {
       p.q_two.push_back(g.members.size() >= 2 ? 1 : 0);
     }
     p.n_qfam = (int64_t)p.q_two.size();
+  }
+
+  // ---- sink-side cost of one source family, per flavour and rank (the flop model below):
+  // every two-sided sink family contributes its block factors once and its solves per
+  // sink, every other sink a shared-row factorisation -----------------------------------
+  std::vector<int64_t> gq1(F, 0), gs1(F, 0), gq2(F, 0), gs2(F, 0);
+  int64_t g_one = 0;
+  for (int64_t Q = 0; Q < p.n_qfam; Q++) {
+    const int64_t sz = p.q_off[Q + 1] - p.q_off[Q];
+    if (!p.q_two[Q]) {
+      g_one += sz;
+      continue;
+    }
+    for (int f = 0; f < F; f++) {
+      if (p.q_rank[Q * F + f] == 2) {
+        gq2[f]++;
+        gs2[f] += sz;
+      } else {
+        gq1[f]++;
+        gs1[f] += sz;
+      }
+    }
+  }
+  auto fam_cost = [&](int f, int rho, int64_t k) {
+    const int n = p.n_f[f];
+    if (n == 0) return 0.0;
+    double c = (double)p.n_snk * (double)k * flops_member(n, rho) + (double)g_one * flops_shared_rows(n, rho);
+    if (rho == 1) {
+      c += (double)gq1[f] * flops_adjugate(n - 1) + (double)gs1[f] * flops_kapply(n);
+      c += (double)gq2[f] * flops_block12(n) + (double)gs2[f] * flops_kapply12(n);
+    } else if (rho == 2) {
+      c += (double)gq1[f] * flops_rank2_block(n) + (double)gs1[f] * flops_kapply2(n);
+      c += (double)gs2[f] * flops_shared_rows(n, rho);
+    } else {
+      c += (double)(gs1[f] + gs2[f]) * flops_shared_rows(n, rho);
+    }
+    return c;
+  };
+
+  // ---- work families: align members, group by compatible changed rows ---------------
+  p.fam_off.assign(1, 0);
+  p.fam_rank.clear();
+  p.fam_rows.clear();
+  p.fam_ref.clear();
+  p.fam_arow.clear();
+  p.mem_term.clear();
+  p.mem_sign.clear();
+  p.mem_par.clear();
+  p.mem_lab.clear();
+  p.src_member.assign(N, -1);
+  p.mem_family.clear();
+  int64_t rank2_blocks = 0, rank3_blocks = 0, rank4p_blocks = 0;
+  p.max_members = 0;
+
+  struct Member {
+    int32_t term;
+    std::vector<Align> al;  // per flavour
+  };
+  struct Group {
+    std::vector<std::vector<int>> R;  // per flavour, ascending changed rows
+    std::vector<int> members;         // indices into the member list
+  };
+  for (auto& ds : dom_sets) {
+    const int32_t v = ds[0];
+    const int32_t* ref = &p.labels_src[(int64_t)v * Tn];
+    std::vector<Member> mems;
+    for (int32_t t : ds) {
+      Member m;
+      m.term = t;
+      for (int f = 0; f < F; f++)
+        m.al.push_back(align(ref + p.off_f[f], &p.labels_src[(int64_t)t * Tn + p.off_f[f]], p.n_f[f]));
+      mems.push_back(std::move(m));
+    }
+    std::vector<Group> groups;
+    if (p.opts.first_fit) {
+      // members in order, each into the first group that stays within dmax changed rows
+      for (int mi = 0; mi < (int)mems.size(); mi++) {
+        bool placed = false;
+        for (auto& g : groups) {
+          if ((int)g.members.size() >= kmax) continue;
+          bool ok = true;
+          std::vector<std::vector<int>> U(F);
+          for (int f = 0; f < F && ok; f++) {
+            std::set<int> u(g.R[f].begin(), g.R[f].end());
+            u.insert(mems[mi].al[f].changed.begin(), mems[mi].al[f].changed.end());
+            U[f].assign(u.begin(), u.end());
+            ok = (int)U[f].size() <= dmax[f];
+          }
+          if (ok) {
+            g.R = U;
+            g.members.push_back(mi);
+            placed = true;
+            break;
+          }
+        }
+        if (!placed) {
+          Group g;
+          g.R.resize(F);
+          for (int f = 0; f < F; f++) g.R[f] = mems[mi].al[f].changed;
+          g.members.push_back(mi);
+          groups.push_back(std::move(g));
+        }
+      }
+    } else {
+      // cost-driven: start from the groups of members with the same changed rows (at most
+      // kmax each), then merge the pair of groups whose merge lowers the plan's flop count
+      // most (a merged family shares one factorisation per sink but may need a higher rank
+      // for all its members), until no merge lowers it
+      std::map<std::vector<std::vector<int>>, std::vector<int>> bysig;
+      for (int mi = 0; mi < (int)mems.size(); mi++) {
+        std::vector<std::vector<int>> sig(F);
+        for (int f = 0; f < F; f++) sig[f] = mems[mi].al[f].changed;
+        bysig[sig].push_back(mi);
+      }
+      for (auto& kv : bysig)
+        for (size_t a = 0; a < kv.second.size(); a += (size_t)kmax) {
+          Group g;
+          g.R = kv.first;
+          g.members.assign(kv.second.begin() + a, kv.second.begin() + std::min(kv.second.size(), a + (size_t)kmax));
+          groups.push_back(std::move(g));
+        }
+      auto gcost = [&](const std::vector<std::vector<int>>& R, int64_t k) {
+        double c = 0.0;
+        for (int f = 0; f < F; f++) c += fam_cost(f, std::max<int>(1, (int)R[f].size()), k);
+        return c;
+      };
+      for (;;) {
+        double best = 0.0;
+        int ba = -1, bb = -1;
+        std::vector<std::vector<int>> bestU;
+        for (int x = 0; x < (int)groups.size(); x++)
+          for (int y = x + 1; y < (int)groups.size(); y++) {
+            const int64_t k = (int64_t)(groups[x].members.size() + groups[y].members.size());
+            if (k > kmax) continue;
+            std::vector<std::vector<int>> U(F);
+            bool ok = true;
+            for (int f = 0; f < F && ok; f++) {
+              std::set<int> u(groups[x].R[f].begin(), groups[x].R[f].end());
+              u.insert(groups[y].R[f].begin(), groups[y].R[f].end());
+              U[f].assign(u.begin(), u.end());
+              ok = (int)U[f].size() <= dmax[f];
+            }
+            if (!ok) continue;
+            const double gain = gcost(groups[x].R, (int64_t)groups[x].members.size()) +
+                                gcost(groups[y].R, (int64_t)groups[y].members.size()) - gcost(U, k);
+            if (gain > best) {
+              best = gain;
+              ba = x;
+              bb = y;
+              bestU = U;
+            }
+          }
+        if (ba < 0) break;
+        groups[ba].R = bestU;
+        groups[ba].members.insert(groups[ba].members.end(), groups[bb].members.begin(), groups[bb].members.end());
+        std::sort(groups[ba].members.begin(), groups[ba].members.end());
+        groups.erase(groups.begin() + bb);
+      }
+      // the dominator's group first, then by first member: a deterministic order
+      std::sort(groups.begin(), groups.end(),
+                [](const Group& x, const Group& y) { return x.members[0] < y.members[0]; });
+    }
+    for (auto& g : groups) {
+      const int64_t W = p.n_fam++;
+      std::vector<int32_t> ranks(F), rows(MHC_MAX_RANK * F, -1), arow(Tn, -1);
+      std::vector<int> eps(F, 0);
+      for (int f = 0; f < F; f++) {
+        const int n = p.n_f[f];
+        std::vector<int> R = g.R[f];
+        if (n == 0) {
+          ranks[f] = 0;
+          continue;
+        }
+        if (R.empty()) R.push_back(n - 1);
+        ranks[f] = (int32_t)R.size();
+        if (R.size() == 2) rank2_blocks++;
+        if (R.size() == 3) rank3_blocks++;
+        if (R.size() >= 4) rank4p_blocks++;
+        for (size_t k = 0; k < R.size(); k++) rows[MHC_MAX_RANK * f + k] = R[k];
+        // [shared rows ascending; changed rows ascending] and the sign of that reordering
+        std::vector<int> order;
+        int a = 0;
+        for (int m = 0; m < n; m++)
+          if (std::find(R.begin(), R.end(), m) == R.end()) {
+            order.push_back(m);
+            arow[p.off_f[f] + a++] = ref[p.off_f[f] + m];
+          }
+        for (int r : R) order.push_back(r);
+        eps[f] = perm_parity(order);
+        g.R[f] = R;
+      }
+      for (int f = 0; f < F; f++) p.fam_rank.push_back(ranks[f]);
+      p.fam_rows.insert(p.fam_rows.end(), rows.begin(), rows.end());
+      p.fam_ref.insert(p.fam_ref.end(), ref, ref + Tn);
+      p.fam_arow.insert(p.fam_arow.end(), arow.begin(), arow.end());
+      for (int mi : g.members) {
+        const Member& m = mems[mi];
+        int parity = 0, bits = 0;
+        std::vector<int32_t> lab(MHC_MAX_RANK * F, -1);
+        for (int f = 0; f < F; f++) {
+          if (p.n_f[f] == 0) continue;
+          const int pf = m.al[f].parity ^ eps[f];
+          parity ^= pf;
+          bits |= pf << f;
+          for (int k = 0; k < ranks[f]; k++) lab[MHC_MAX_RANK * f + k] = m.al[f].aligned[g.R[f][k]];
+        }
+        p.mem_lab.insert(p.mem_lab.end(), lab.begin(), lab.end());
+        p.src_member[m.term] = (int32_t)p.mem_term.size();
+        p.mem_term.push_back(m.term);
+        p.mem_sign.push_back(parity ? -1 : 1);
+        p.mem_par.push_back(bits);
+        p.mem_family.push_back((int32_t)W);
+      }
+      p.fam_off.push_back((int64_t)p.mem_term.size());
+      p.max_members = std::max(p.max_members, (int)g.members.size());
+    }
   }
 
   // ---- statistics -------------------------------------------------------------------

@@ -45,7 +45,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("tau_parent", ctypes.c_double), ("tau_child", ctypes.c_double),
                 ("sink_tile", ctypes.c_int32), ("rank2", ctypes.c_int32),
                 ("max_family", ctypes.c_int32), ("one_sided", ctypes.c_int32),
-                ("rank3", ctypes.c_int32), ("max_rank", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("rank3", ctypes.c_int32), ("max_rank", ctypes.c_int32), ("first_fit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Stats(ctypes.Structure):

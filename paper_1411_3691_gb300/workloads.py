@@ -74,11 +74,13 @@ def add_twins(rng, S: np.ndarray, n_twins: int = 8, noise: float = 1e-13):
 
 
 def make_side(rng, n_f, L_f, family_sizes, two_row_frac=0.0, forced_frac=0.0,
-              n_ordinary=None, twin_origin=None, three_row_frac=0.0, more_rows=None):
+              n_ordinary=None, twin_origin=None, three_row_frac=0.0, more_rows=None, mixed_rows=False):
     """Term list of one side; returns (labels int32 [N, sum n_f], info dict).  more_rows:
     {k: fraction} (every flavour) or a list of such dicts (one per flavour) for families
     whose members change k >= 4 rows of a flavour (drawn only when given, so the other
-    workloads keep their random streams)."""
+    workloads keep their random streams).  mixed_rows: every member k > 0 of a family
+    changes one row of its own choosing in each flavour (the family's rows are then all
+    rows its members change), instead of the family's common rows."""
     F = len(n_f)
     Tn = int(sum(n_f))
     N = int(sum(family_sizes))
@@ -122,9 +124,14 @@ def make_side(rng, n_f, L_f, family_sizes, two_row_frac=0.0, forced_frac=0.0,
                 new = np.concatenate([rng.permutation(pool),
                                       rng.choice(pool, size=need - pool.size, replace=True)])
             new = new.astype(np.int32).reshape(max(size - 1, 0), len(rr)) if size > 1 else np.zeros((0, len(rr)), np.int32)
+            own = [int(rng.integers(n)) for _ in range(size - 1)] if mixed_rows else None
+            if mixed_rows:
+                fam_rows[-1] = tuple(sorted(set(own)))
             for k in range(size):
                 tup = parent.copy()
-                if k > 0:
+                if k > 0 and mixed_rows:
+                    tup[own[k - 1]] = new[k - 1, 0]
+                elif k > 0:
                     for t, r in enumerate(rr):
                         tup[r] = new[k - 1, t]
                     if forced_frac > 0 and twin_origin is not None and rng.random() < forced_frac:
@@ -147,7 +154,7 @@ def make_side(rng, n_f, L_f, family_sizes, two_row_frac=0.0, forced_frac=0.0,
 
 
 def make_workload(name, n_f, L_f, fam_src, fam_snk, diag=2.0, seed=0, two_row_frac=0.0,
-                  forced_frac=0.0, twins=0, three_row_frac=0.0, more_rows=None):
+                  forced_frac=0.0, twins=0, three_row_frac=0.0, more_rows=None, mixed_rows=False):
     ss = np.random.SeedSequence(seed)
     r_S, r_src, r_snk, _ = [np.random.default_rng(s) for s in ss.spawn(4)]
     S = [make_S(r_S, int(L), diag) for L in L_f]
@@ -157,7 +164,7 @@ def make_workload(name, n_f, L_f, fam_src, fam_snk, diag=2.0, seed=0, two_row_fr
         twin_origin = [add_twins(r_S, s, twins) for s in S]
         n_ord = [int(L) - twins for L in L_f]
     ls, info_s = make_side(r_src, n_f, L_f, fam_src, two_row_frac, forced_frac, n_ord, twin_origin,
-                           three_row_frac, more_rows)
+                           three_row_frac, more_rows, mixed_rows)
     lk, info_k = make_side(r_snk, n_f, L_f, fam_snk, two_row_frac, 0.0, n_ord, twin_origin, three_row_frac)
     ws = r_src.normal(size=ls.shape[0])
     wk = r_snk.normal(size=lk.shape[0])

@@ -44,7 +44,7 @@ def gpu_backward(M, plan, S, g):
 def check_vs_oracle(M, w, opts=None, threads=8):
     if opts is None:
         opts = M.default_opts()
-        opts.rank2 = 1 if w.name in ("tc", "r2") else 0
+        opts.rank2 = 1 if w.name in ("tc", "r2", "mr") else 0
     plan = M.Plan.from_workload(w, opts)
     if w.name == "r2":
         assert plan.stats()["rank2_family_flavours"] > 0
@@ -88,6 +88,8 @@ CASES = {
                                                [5, 4], [6, 3], seed=51),
     "n32": lambda: wl.make_workload("n32", [32], [64], [3, 2], [6, 4], seed=12),
     "single_terms": lambda: wl.make_workload("one", [3, 2], [10, 8], [1], [1], seed=53),
+    "mixed_rows": lambda: wl.make_workload("mr", [12, 10], [60, 48], [9, 7, 8], [5, 6, 4], seed=97,
+                                           mixed_rows=True),
     "two_row_families_n18": lambda: wl.make_workload("r2", [18, 18], [96, 96], [8, 6], [7, 5], diag=3.0,
                                                      seed=43, two_row_frac=0.5),
 }

@@ -67,6 +67,9 @@ def small_cases():
         "eight_flavours": wl.make_workload("f8", [2, 3, 1, 4, 2, 3, 1, 2], [12, 16, 8, 20, 12, 16, 8, 12],
                                            [5, 4], [6, 3], seed=51),
         "single_terms": wl.make_workload("one", [3, 2], [10, 8], [1], [1], seed=53),
+        # members changing rows of their own: families split and merged by the flop count
+        "mixed_rows": wl.make_workload("mr", [12, 18], [60, 96], [9, 12, 7, 16], [5, 6, 4, 20], diag=3.0,
+                                       seed=97, mixed_rows=True),
     }
 
 

@@ -92,7 +92,7 @@ def _walk(M, w, plan):
 
 
 @pytest.mark.parametrize("name", ["deuteron", "helium4", "large", "mixed", "three_rows", "four_rows",
-                                  "five_rows"])
+                                  "five_rows", "mixed_rows", "mixed_rows_first_fit"])
 def test_plan_walk_matches_oracle(M, name):
     if name == "deuteron":
         w = wl.deuteron(scale=6 / 64)
@@ -105,6 +105,8 @@ def test_plan_walk_matches_oracle(M, name):
                              two_row_frac=0.5, forced_frac=0.2, twins=8)
     elif name == "mixed":
         w = wl.make_workload("mixed", [3, 0, 7], [24, 5, 30], [5, 1, 3, 8], [3, 3], seed=9, two_row_frac=0.3)
+    elif name.startswith("mixed_rows"):
+        w = wl.make_workload("mr", [12, 6], [60, 48], [9, 12, 7], [5, 6, 4], seed=97, mixed_rows=True)
     elif name == "four_rows":
         w = wl.make_workload("r4", [18, 12], [96, 60], [5, 4, 4, 3], [4, 3], diag=3.0, seed=91,
                              two_row_frac=0.3, more_rows=[{4: 0.6}, {}])
@@ -117,6 +119,7 @@ def test_plan_walk_matches_oracle(M, name):
     opts = M.default_opts()
     opts.rank3 = 1 if name == "three_rows" else 0
     opts.max_rank = {"four_rows": 4, "five_rows": 5}.get(name, 0)
+    opts.first_fit = 1 if name == "mixed_rows_first_fit" else 0
     plan = M.Plan.from_workload(w, opts)
     if name == "three_rows":
         assert plan.stats()["rank3_family_flavours"] > 0
@@ -228,6 +231,8 @@ def test_greedy_dominating_set(M, seed):
     assert st["graph_edges"] == sum(len(a) for a in adj) // 2
     opt = _min_dominating(adj)
     assert opt <= len(doms)
+    # the greedy set against the exact minimum (Sec. 3: minimum dominating set is NP-complete)
+    print(f"greedy {len(doms)} / exact {opt} = {len(doms) / opt:.3f}")
     # families are dominator + neighbours: every member differs from its reference in at
     # most one label per flavour
     fam = plan.families()
@@ -345,3 +350,25 @@ def test_sink_families_two_sided(M, name):
                 shared = sk["labels"][pos][:, off[f]:off[f] + keep]
                 assert np.all(shared == shared[0])
     plan.close()
+
+
+@pytest.mark.parametrize("n,L", [(12, 60), (18, 96)])
+def test_cost_grouping_lowers_flops(M, n, L):
+    """Families whose members each change a row of their own (Sec. 3's dominating set with
+    neighbours in any position): splitting each dominated set by the plan's flop count
+    gives fewer flops per call than first fit, which merges rows into rank-2 families for
+    every member; every term stays a member of exactly one family."""
+    w = wl.make_workload("mixed", [n, n], [L, L], [32] * 16, [16] * 32, seed=7, mixed_rows=True)
+    res = {}
+    for ff in (1, 0):
+        opts = M.default_opts()
+        opts.first_fit = ff
+        plan = M.Plan.from_workload(w, opts)
+        res[ff] = plan.stats()
+        fam = plan.families()
+        assert sorted(fam["term"].tolist()) == list(range(plan.n_src))
+        plan.close()
+    ratio = res[0]["flops_per_call"] / res[1]["flops_per_call"]
+    print(f"n = {n}: cost grouping / first fit flops = {ratio:.4f}")
+    assert res[0]["dominators"] == res[1]["dominators"]
+    assert ratio < 0.99
