@@ -64,6 +64,12 @@ def parse():
                          "forced members / at 1/8 scale per side (for profiler captures)")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the selected workload only (no sub-objects, no CPU baseline)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the adjoint of the selected workload alone and print its sub-object "
+                         "(for profiler captures)")
+    ap.add_argument("--batch", action="store_true",
+                    help="time the 64-correlator batch alone and print its sub-object (for profiler "
+                         "captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help=argparse.SUPPRESS)  # tests: shrink the workload
     ap.add_argument("--cpu-pairs", type=int, default=100000,
@@ -283,6 +289,16 @@ def run_gpu(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if args.adjoint or args.batch:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        peak = mhc.mhc_fp64_peak(250000) / 1e12
+        stream = torch.cuda.current_stream()
+        if args.adjoint:
+            r = time_adjoint(mhc, workload(rank, args.workload), flush, stream, peak, steps=args.steps)
+        else:
+            r = time_batch(mhc, flush, stream, peak, reps=args.steps)
+        print(json.dumps({"adjoint" if args.adjoint else "batch": r}), flush=True)
+        return
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -495,7 +511,8 @@ def time_adjoint(mhc, w, flush, stream, peak, steps=10):
     res = {"workload": w.name, "ms_per_step": ms, "forward_ms_per_step": fwd_ms, "ratio_vs_forward": ms / fwd_ms,
            "pairs_per_s": w.pairs / (ms * 1e-3), "tflops": bflops / (ms * 1e-3) / 1e12,
            "frac_of_fp64_peak": bflops / (ms * 1e-3) / 1e12 / peak, "flops_per_step": bflops,
-           "outputs": "dS_f (2 x 48 x 48 complex), dw_src [4096], dw_snk [4096]; L = Re C",
+           "outputs": f"dS_f ({len(w.n_f)} x {w.L_f[0]} x {w.L_f[0]} complex), dw_src [{len(w.w_src)}], "
+                      f"dw_snk [{len(w.w_snk)}]; L = Re C",
            # block factors and B^-1 (two-sided plans), the adjoint kernel, one dS finalize per
            # flavour, the two weight finalizes
            "gpu_launches_per_step": (3 if st["two_sided_blocks"] > 0 else 1) + len(S) + 2}
@@ -512,9 +529,28 @@ def time_batch(mhc, flush, stream, peak, count=64, reps=10):
     plans = [mhc.Plan.from_workload(w) for w in items]
     S = [[torch.from_numpy(s).cuda() for s in w.S] for w in items]
     pairs = sum(w.pairs for w in items)
+    # the autotuner's cache in a file of this run (the first create times every class, the
+    # second finds each class's tile in the cache)
+    cache = tempfile.NamedTemporaryFile(suffix=".jsonl", delete=False)
+    cache.close()
+    os.unlink(cache.name)
+    saved = os.environ.get("MHC_TUNE_CACHE")
+    os.environ["MHC_TUNE_CACHE"] = cache.name
+    t0 = time.perf_counter()
+    first = mhc.mhc_batch_create([p.handle for p in plans])
+    create_s = time.perf_counter() - t0
+    tiles, _, tune_ms = mhc.mhc_batch_shape(first)
+    mhc.mhc_batch_destroy(first)
     t0 = time.perf_counter()
     batch = mhc.mhc_batch_create([p.handle for p in plans])
-    create_s = time.perf_counter() - t0
+    create2_s = time.perf_counter() - t0
+    tiles2, cached, _ = mhc.mhc_batch_shape(batch)
+    if saved is None:
+        del os.environ["MHC_TUNE_CACHE"]
+    else:
+        os.environ["MHC_TUNE_CACHE"] = saved
+    if os.path.exists(cache.name):
+        os.unlink(cache.name)
     T, n_items = mhc.mhc_batch_info(batch)
     outs = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in items]
     mhc.mhc_batch_correlator(batch, S, outs)
@@ -548,7 +584,10 @@ def time_batch(mhc, flush, stream, peak, count=64, reps=10):
             "tflops": flops / (batch_ms * 1e-3) / 1e12, "frac_of_fp64_peak": flops / (batch_ms * 1e-3) / 1e12 / peak,
             "sequential_ms": seq_ms, "sequential_pairs_per_s": pairs / (seq_ms * 1e-3),
             "speedup_vs_sequential": seq_ms / batch_ms, "reps": reps, "tile": T, "work_items": n_items,
-            "batch_create_s": create_s, "graph": True}
+            "tiles_by_n_class": {"n<=8": tiles[0], "n<=18": tiles[1], "n<=32": tiles[2]},
+            "tuning_ms_by_n_class": {"n<=8": tune_ms[0], "n<=18": tune_ms[1], "n<=32": tune_ms[2]},
+            "batch_create_s": create_s, "batch_create_cached_s": create2_s,
+            "second_create_from_cache": [int(c) for c, t in zip(cached, tiles2) if t], "graph": True}
 
 
 def run_fp64_peak(args):
