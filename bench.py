@@ -44,11 +44,16 @@ UNIT = "pairs/s"
 # FP64 peak from unit counts and clocks: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
 NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of every kernel of one forward call, from one
-# ncu capture per workload (the large nucleus: a 1/8-per-side copy, 1/64 of the pairs and of the
-# block factors, scaled by 64).  None where no capture of the current kernels exists.
+# ncu capture of the current kernels.  The large nucleus holds 9.7 GB of block factors, too much
+# for a multi-metric capture, so its 1/8-per-side copy (--workload large_small: 1/64 of the pairs
+# and of the (family, sink family) blocks) was captured and the sum scaled by 64: 165.9 MB read
+# + 99.5 MB written per call of the copy (kfac_kernel, kfac_group_kernel, three fwd_kernel
+# launches, reduce_kernel).
 TRAFFIC = {
-    "large": None,
-    "he4": None,
+    "large": {"bytes": 265.40e6 * 64,
+              "source": "ncu dram bytes of every kernel of one call of the 1/8-per-side copy "
+                        "(--workload large_small), x 64"},
+    "he4": {"bytes": 69.93e6, "source": "ncu dram bytes of the fwd_kernel launch of one call"},
 }
 
 
