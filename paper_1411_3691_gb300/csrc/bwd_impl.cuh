@@ -1033,10 +1033,14 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
       const int rho = a.fam_rank[(int64_t)W * a.F + f];
       const int sig = qtwo ? a.q_rank[(int64_t)Q * a.F + f] : 0;
-      if (qtwo && (rho == 1 || sig == 1) && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+      if (qtwo && (rho == 1 || sig == 1 || (rho == 2 && sig == 2)) &&
+          !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
         // two-sided block: y (z1, z2 for two-row families) from the stored factors
         const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
-        if (rho == 2)
+        if (rho == 2 && sig == 2)
+          dev::dispatch_kapply22<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+        else if (rho == 2)
           dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
         else if (sig == 2)

@@ -419,6 +419,67 @@ __device__ __forceinline__ void kapply2(const cd* __restrict__ S, int L, int n_r
   *ey = expo(sd) + 2 * ez;
 }
 
+// Two-sided update of a two-row family against a two-column sink family: the n-2 shared rows
+// and the n-2 shared columns give the square block B, factorised once per block (the layout
+// of kapply with n-1 in place of n: LU[M][M] | perm[M] | -det B | det B, M = n - 2).  The
+// shared rows are A = [B | a1(j) a2(j)] (the sink's changed columns last), whose null
+// vectors are z_t = [-B^{-1} a_t(j) ; e_t], and det [A ; b1 ; b2] = det(B) det(B' Z) as in
+// shared_rows with RHO = 2: two triangular solves per sink instead of a factorisation.
+template <int NC, int NFIX>
+__device__ __forceinline__ void kapply22(const cd* __restrict__ S, int L, int n_rt,
+                                         const int32_t* __restrict__ arow,
+                                         const int32_t* __restrict__ colp, const cd* __restrict__ K,
+                                         cd* __restrict__ Y, int ys, int* ey) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const int M = n - 2;
+  constexpr int MC = NC - 2 > 0 ? NC - 2 : 1;
+  const int c1 = colp[n - 2], c2 = colp[n - 1];
+  cd x1[MC], x2[MC];
+#pragma unroll UNR
+  for (int i = 0; i < M; i++) {  // P a_t, then L^{-1}
+    const int pr = (int)__ldg(&K[M * M + i].x);
+    const cd* row = S + (size_t)arow[pr] * L;
+    cd w1 = ldS(row + c1), w2 = ldS(row + c2);
+#pragma unroll UNR
+    for (int t = 0; t < i; t++) {
+      const cd l = __ldg(K + i * M + t);
+      w1 = cfms(l, x1[t], w1);
+      w2 = cfms(l, x2[t], w2);
+    }
+    x1[i] = w1;
+    x2[i] = w2;
+  }
+#pragma unroll UNR
+  for (int i = M - 1; i >= 0; i--) {  // U^{-1}
+    cd w1 = x1[i], w2 = x2[i];
+#pragma unroll UNR
+    for (int t = i + 1; t < M; t++) {
+      const cd u = __ldg(K + i * M + t);
+      w1 = cfms(u, x1[t], w1);
+      w2 = cfms(u, x2[t], w2);
+    }
+    const cd r = __ldg(K + i * M + i);
+    x1[i] = cmul(w1, r);
+    x2[i] = cmul(w2, r);
+  }
+  int ez = 0;
+#pragma unroll UNR
+  for (int u = 0; u < M; u++) {
+    const cd z1 = cneg(x1[u]), z2 = cneg(x2[u]);
+    Y[u * ys] = z1;
+    Y[(n + u) * ys] = z2;
+    ez = max(ez, max(expo(z1), expo(z2)));
+  }
+  Y[M * ys] = make_double2(1.0, 0.0);
+  Y[(M + 1) * ys] = make_double2(0.0, 0.0);
+  Y[(n + M) * ys] = make_double2(0.0, 0.0);
+  Y[(n + M + 1) * ys] = make_double2(1.0, 0.0);
+  const cd sd = __ldg(K + M * M + M + 1);
+  Y[2 * n * ys] = sd;
+  *ey = expo(sd) + 2 * ez;
+}
+
 // Factorisation of one two-sided block (see kapply / kapply2), one thread per block: rows
 // S[arow[i]], i < M, columns S[.][scol[u]], u < M (+ the extra column u = M for RHO = 2).
 // Partial pivoting with the shared_rows rule.  Returns true when the pivot guard fires.

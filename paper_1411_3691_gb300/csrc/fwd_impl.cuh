@@ -278,9 +278,13 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
     const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
     const int sig = qtwo ? a.q_rank[(int64_t)Q * a.F + f] : 0;
-    if (qtwo && (rho == 1 || sig == 1) && !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
+    if (qtwo && (rho == 1 || sig == 1 || (rho == 2 && sig == 2)) &&
+        !a.kguard[((int64_t)W * a.n_q + Q) * a.F + f]) {
       const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
-      if (rho == 2)
+      if (rho == 2 && sig == 2)
+        dev::dispatch_kapply22<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
+                                      Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+      else if (rho == 2)
         dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
                                      Y + (size_t)a.yoff[f] * T, T, &ey[f]);
       else if (sig == 2)
@@ -597,8 +601,10 @@ __device__ __forceinline__ void kfac_group_one(const FwdArgs& a, int64_t t) {
   const int32_t* scol = a.snk_pos + (int64_t)a.q_off[Q] * a.Tn + a.off_f[f];
   dev::cd* K = const_cast<dev::cd*>(a.kbuf) + wq * a.kstride + a.koff[f];
   bool gd;
-  if ((rho == 2 && sig == 2) || rho >= 3)  // one-sided update for these blocks
+  if (rho >= 3)  // one-sided update for these blocks
     gd = true;
+  else if (rho == 2 && sig == 2)  // the (n-2) x (n-2) shared block, kapply's layout (kapply22)
+    gd = dev::group_kfac_block<KG::G>(S, L, n - 1, 1, arow, scol, K, a.kp, g, gm, Bs, Ws, Ps);
   else if (sig == 2)
     gd = dev::group_kfac_block12<KG::G>(S, L, n, arow, scol, K, a.kp, g, gm, Bs, Ps);
   else

@@ -183,6 +183,17 @@ __device__ __forceinline__ void dispatch_kapply2(int n, const cd* S, int L, cons
 }
 
 template <int NCMAX>
+__device__ __forceinline__ void dispatch_kapply22(int n, const cd* S, int L, const int32_t* arow,
+                                                  const int32_t* col, const cd* K, cd* Y, int ys,
+                                                  int* ey) {
+  if constexpr (NCMAX >= 18) {
+    if (n == 12) { kapply22<12, 12>(S, L, 12, arow, col, K, Y, ys, ey); return; }
+    if (n == 18) { kapply22<18, 18>(S, L, 18, arow, col, K, Y, ys, ey); return; }
+  }
+  kapply22<NCMAX, 0>(S, L, n, arow, col, K, Y, ys, ey);
+}
+
+template <int NCMAX>
 __device__ __forceinline__ void dispatch_kapply12(int n, const cd* S, int L, const int32_t* arow,
                                                   const int32_t* col, const cd* K, cd* Y, int ys,
                                                   int* ey) {

@@ -129,6 +129,7 @@ double flops_fresh_lu(int n);               // one fresh partial-pivot LU determ
 double flops_kapply(int n);                 // y = [-det(B) B^{-1} a; det B] for one sink
 double flops_adjugate(int m);               // LU factors of one m x m two-sided block
 double flops_kapply2(int n);                // z2 for one sink (two-row family)
+double flops_kapply22(int n);               // z1, z2 for one sink (two-row x two-column block)
 double flops_rank2_block(int n);            // LU factors and -U1^{-1}u of one two-row block
 double flops_block12(int n);                // LU factors of one (one-row, two-column) block
 double flops_kapply12(int n);               // y for one sink of a two-column sink family

@@ -160,6 +160,14 @@ double flops_kapply2(int n) {
   return 8.0 * M * (M - 1) + 6.0 * M;
 }
 
+// two-row family x two-column sink family, per sink: two forward and two backward solves
+// with the stored factors of the (n-2) x (n-2) shared block (M = n - 2)
+double flops_kapply22(int n) {
+  if (n < 3) return 0.0;
+  const double M = n - 2;
+  return 2.0 * (8.0 * M * (M - 1) + 6.0 * M);
+}
+
 // two-row family, per block: LU of the M shared rows over M + 1 shared columns, -U1^{-1} u
 double flops_rank2_block(int n) {
   if (n < 2) return 0.0;
@@ -488,7 +496,7 @@ mhc_status build_plan(Plan& p) {
       c += (double)gq2[f] * flops_block12(n) + (double)gs2[f] * flops_kapply12(n);
     } else if (rho == 2) {
       c += (double)gq1[f] * flops_rank2_block(n) + (double)gs1[f] * flops_kapply2(n);
-      c += (double)gs2[f] * flops_shared_rows(n, rho);
+      c += (double)gq2[f] * flops_adjugate(n - 2) + (double)gs2[f] * flops_kapply22(n);
     } else {
       c += (double)(gs1[f] + gs2[f]) * flops_shared_rows(n, rho);
     }
@@ -723,8 +731,9 @@ mhc_status build_plan(Plan& p) {
         two_blocks += qc1[f] + qc2[f];
       } else if (rho == 2) {
         fl += (double)qc1[f] * flops_rank2_block(n) + (double)qs1[f] * flops_kapply2(n);
-        fl += (double)qs2[f] * flops_shared_rows(n, rho);  // two changed rows and columns
-        two_blocks += qc1[f];
+        // two changed rows and columns: the (n-2) x (n-2) shared block once, two solves per sink
+        fl += (double)qc2[f] * flops_adjugate(n - 2) + (double)qs2[f] * flops_kapply22(n);
+        two_blocks += qc1[f] + qc2[f];
       } else {  // three changed rows: every sink one-sided
         fl += (double)(qs1[f] + qs2[f]) * flops_shared_rows(n, rho);
       }
