@@ -18,6 +18,9 @@ the slowest rank.
 Sub-objects of the line (rank 0, N = 1 unless --headline-only):
   one_sided  the same workload planned with opts.one_sided = 1 (Sec. 3 as printed: source
              families only), time and fraction of the FP64 peak;
+  row_difference  the same workload with opts.row_difference = 1 (one-row members that fail
+             the lemma guard are updated from the difference of their row and the nearest
+             shared row before a refactor), time and fraction of the FP64 peak;
   configs    the deuteron-like (512 x 512, n = 3) and He-4-like (4096 x 4096, n = 6) forward
              calls, the 64-correlator batch (one CUDA graph vs 64 sequential calls) and the
              adjoint on the He-4-like shapes (backward vs forward time).
@@ -76,6 +79,8 @@ def parse():
                     help="time the 64-correlator batch alone and print its sub-object (for profiler "
                          "captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--row-difference", action="store_true",
+                    help="plan with opts.row_difference = 1 (recorded in config)")
     ap.add_argument("--scale", type=float, default=1.0, help=argparse.SUPPRESS)  # tests: shrink the workload
     ap.add_argument("--cpu-pairs", type=int, default=100000,
                     help="seeded (i, j) pairs the oracle evaluates for cpu_baseline / --impl reference")
@@ -311,7 +316,9 @@ def run_gpu(args):
         pg = dist
     w = workload(rank, args.workload)
     extras = not args.headline_only and world == 1 and rank == 0
-    plan = mhc.Plan.from_workload(w)
+    hopts = mhc.default_opts()
+    hopts.row_difference = 1 if args.row_difference else 0
+    plan = mhc.Plan.from_workload(w, hopts)
     st = plan.stats()
     S = [torch.from_numpy(s).cuda() for s in w.S]
     out = torch.empty(2, dtype=torch.float64, device="cuda")
@@ -356,6 +363,7 @@ def run_gpu(args):
     # plus the refactor path as the device counted it -- over the whole step's device time
     # (every launch of the call), against the FP64 peak measured above
     refactor_pairs = (st["refactor_parent"] + st["refactor_child"]) / max(args.steps, 1)
+    rowdiff_pairs = st["row_difference"] / max(args.steps, 1)
     refactor_flops = st["refactor_flops"] / max(args.steps, 1)
     flops = st["flops_per_call"] + refactor_flops
     achieved = flops / (ms_per_step * 1e-3) / 1e12
@@ -389,9 +397,10 @@ def run_gpu(args):
     C = [float(out[0].item()), float(out[1].item())]
 
     launches = forward_launches(plan, w, st)
-    one_sided = configs = None
+    one_sided = rowdiff = configs = None
     if extras:
         one_sided = time_one_sided(mhc, w, S, out, flush, stream, ms_per_step, peak)
+        rowdiff = time_row_difference(mhc, w, S, out, flush, stream, ms_per_step, peak)
     plan.close()
     if extras:
         configs = {
@@ -410,6 +419,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(w, st), **{
                 "parallelism": f"{world} independent correlators (one per GPU)",
+                "row_difference": bool(args.row_difference),
                 "l2": "flushed between timed steps (256 MiB write outside the events); the call's "
                       "block factors exceed L2"}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -426,7 +436,9 @@ def run_gpu(args):
             "gpu_launches": launches * args.steps,
             "clocks": clocks,
             "refactors_per_step": refactor_pairs,
+            "row_difference_per_step": rowdiff_pairs,
             "one_sided": one_sided,
+            "row_difference": rowdiff,
             "configs": configs,
             "C": C,
         }
@@ -451,6 +463,24 @@ def time_one_sided(mhc, w, S, out, flush, stream, two_ms, peak):
     return {"ms_per_step": ms, "pairs_per_s": w.pairs / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12,
             "frac_of_fp64_peak": flops / (ms * 1e-3) / 1e12 / peak, "flops_per_step": flops,
             "two_sided_speedup": ms / two_ms}
+
+
+def time_row_difference(mhc, w, S, out, flush, stream, ref_ms, peak, steps=5):
+    """The same workload with opts.row_difference = 1: one-row members that fail the lemma
+    guard take the row-difference update (det [A; b] = det [A; b - a_r]) and are refactored
+    only if it fails its own guard."""
+    opts = mhc.default_opts()
+    opts.row_difference = 1
+    plan = mhc.Plan.from_workload(w, opts)
+    ms = time_forward(plan, S, out, flush, stream, steps=steps, warmup=2)
+    st = plan.stats()
+    flops = st["flops_per_call"] + st["refactor_flops"] / steps
+    plan.close()
+    return {"ms_per_step": ms, "pairs_per_s": w.pairs / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12,
+            "frac_of_fp64_peak": flops / (ms * 1e-3) / 1e12 / peak, "flops_per_step": flops,
+            "refactors_per_step": (st["refactor_parent"] + st["refactor_child"]) / steps,
+            "row_difference_per_step": st["row_difference"] / steps,
+            "speedup_vs_refactor": ref_ms / ms}
 
 
 def time_config(mhc, w, flush, stream, peak, steps=20, opts=None):

@@ -97,7 +97,13 @@ typedef struct {
                           members) most lowers the plan's flop count is merged
                           until no merge lowers it; 1: first fit in term order
                           (each member joins the first family it fits).        0     */
-  int32_t reserved[4];
+  int32_t row_difference; /* 0: a member that fails the lemma guard is refactored from
+                          scratch; 1: a one-row member is first updated from the
+                          difference of its row and the nearest shared row
+                          (det [A; b] = det [A; b - a_r]: no cancellation when b
+                          nearly repeats a_r), guarded again, and refactored only
+                          if that guard fails too.                              0     */
+  int32_t reserved[3];
 } mhc_plan_opts;
 
 /* Planner and run statistics. */
@@ -128,6 +134,9 @@ typedef struct {
                                     flops_per_call; a group of pairs refactored together
                                     counts its shared elimination once)                */
   int64_t rank4plus_family_flavours; /* (family, flavour) blocks updated at rank >= 4   */
+  int64_t row_difference;        /* (member, sink, flavour) that failed the lemma guard and
+                                    took the row-difference update instead of a refactor
+                                    (mhc_plan_opts.row_difference = 1)                 */
 } mhc_stats;
 
 /* Thread-local message describing the last failure of this thread's last call. */
@@ -293,7 +302,8 @@ mhc_status mhc_correlator_noalloc(mhc_plan_t plan, const double* const* S_f,
  *   dets_dev     : device float64 [n_pairs][F][2], det of each flavour block in the
  *                  terms' own label order, written
  *   path_dev     : device int32 [n_pairs] or NULL; bit f set when flavour f of the
- *                  pair was refactored from scratch by a guard
+ *                  pair was refactored from scratch by a guard, bit 8 + f when it took
+ *                  the row-difference update (see mhc_plan_opts.row_difference)
  * Indices out of range give MHC_EINVAL through the device status (mhc_get_status).
  */
 mhc_status mhc_pair_dets(mhc_plan_t plan, const double* const* S_f, int64_t n_pairs,

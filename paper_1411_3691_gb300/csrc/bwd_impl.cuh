@@ -360,8 +360,8 @@ __device__ __forceinline__ void cof_pass(const FwdArgs& a, const BwdArgs& B, int
 // shared block is sd [ s (u_m; 0) - sum_v (u_m . E_v) z_v ],  u_m = A1^{-1} e_m, O(n) per
 // member and no division by det G.  Writes the shared block to Mst (row-major
 // (n-k) x n) and member row a's coefficients on z_v, gamma sd adj(D)[v][a], to
-// R[c][a k + v][T].  When the shared rows fail the pivot guard the block is not
-// differentiated: the outputs are zero and the status reports it.
+// R[c][a k + v][T].  When the shared rows fail the pivot guard the same outputs come from
+// cof_passk_guarded (complete pivoting, or signed minors for rank-deficient shared rows).
 template <int RK>
 __device__ __forceinline__ void adjugate(const cd (&D)[RK][RK], cd (&adj)[RK][RK], cd* det) {
   if constexpr (RK == 2) {
@@ -1025,10 +1025,10 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
 
     // ---- pass 1: cached solves, member dets (fresh where guarded), dw partials --------
     unsigned pguard = 0;
-    int ey[MHC_FMAX];
+    dev::FlavourScales eys;
     for (int f = 0; f < a.F; f++) {
       const int n = a.n_f[f];
-      ey[f] = 0;
+      int ey = 0;
       if (n == 0) continue;
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
       const int rho = a.fam_rank[(int64_t)W * a.F + f];
@@ -1039,21 +1039,22 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
         const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
         if (rho == 2 && sig == 2)
           dev::dispatch_kapply22<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey);
         else if (rho == 2)
           dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                       Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+                                       Ysm + (size_t)a.yoff[f] * T + tid, T, &ey);
         else if (sig == 2)
           dev::dispatch_kapply12<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+                                        Ysm + (size_t)a.yoff[f] * T + tid, T, &ey);
         else
           dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                      Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f]);
+                                      Ysm + (size_t)a.yoff[f] * T + tid, T, &ey);
       } else {
         const bool g = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
-                                                   Ysm + (size_t)a.yoff[f] * T + tid, T, &ey[f], a.kp);
+                                                   Ysm + (size_t)a.yoff[f] * T + tid, T, &ey, a.kp);
         pguard |= (unsigned)g << f;
       }
+      eys.set(f, ey);
     }
     double2 accj = make_double2(0.0, 0.0);
     for (int c = 0; c < kW; c++) {
@@ -1066,9 +1067,20 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
           bool fail = (pguard >> f) & 1;
           const int32_t* col = cols + a.off_f[f];
           const int rho = a.fam_rank[(int64_t)W * a.F + f];
+          const bool lemma = !fail;  // the member's own guard decides (not the pivot guard)
           if (!fail)
             d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK,
-                                            col, Ysm + (size_t)a.yoff[f] * T + tid, T, ey[f], a.kc, &fail);
+                                            col, Ysm + (size_t)a.yoff[f] * T + tid, T, eys.get(f), a.kc, &fail);
+          if (fail && lemma && rho == 1 && n >= 2 && a.rowdiff) {  // as in the forward
+            bool f2 = true;
+            const cd d2 = dev::rowdiff_det(a.S[f], a.L_f[f], n, a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK],
+                                           a.fam_arow + (int64_t)W * a.Tn + a.off_f[f], col,
+                                           Ysm + (size_t)a.yoff[f] * T + tid, T, eys.get(f), a.kc, &f2);
+            if (!f2) {
+              d = d2;
+              fail = false;
+            }
+          }
           if (fail) {
             dev::member_rows(a, W, m, f, rho, rows);
             d = dev::dispatch_fresh<NCMAX>(n, a.S[f], a.L_f[f], rows, col);

@@ -320,6 +320,105 @@ __device__ __forceinline__ cd member_det(const cd* __restrict__ S, int L, int n_
   }
 }
 
+// Rank-2 members against a two-sided block with one changed column (kapply2): the first null
+// vector z1 = [-U1^{-1} u ; 1 ; 0] is the same for every sink of the sink family, so the dots
+// b1 . z1 and b2 . z1 of a member are too (the sink's changed column meets z1's zero).
+// member_dots_z1 forms them (in member_det's order, so the results are bitwise the same) and
+// member_det_z1 finishes the member's determinant from them with b1 . z2, b2 . z2.
+template <int NC, int NFIX>
+__device__ __forceinline__ void member_dots_z1(const cd* __restrict__ S, int L, int n_rt,
+                                               const int32_t* __restrict__ lab,
+                                               const int32_t* __restrict__ colp,
+                                               const cd* __restrict__ Y, int ys, cd* d11, cd* d21) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const cd* r1 = S + (size_t)lab[0] * L;
+  const cd* r2 = S + (size_t)lab[1] * L;
+  cd a = make_double2(0.0, 0.0), b = a;
+#pragma unroll UNR
+  for (int q = 0; q < n; q++) {
+    const int c = colp[q];
+    const cd z1 = Y[q * ys];
+    a = cfma(ldS(r1 + c), z1, a);
+    b = cfma(ldS(r2 + c), z1, b);
+  }
+  *d11 = a;
+  *d21 = b;
+}
+
+template <int NC, int NFIX>
+__device__ __forceinline__ cd member_det_z1(const cd* __restrict__ S, int L, int n_rt,
+                                            const int32_t* __restrict__ lab,
+                                            const int32_t* __restrict__ colp, const cd* __restrict__ Y,
+                                            int ys, int ey, int kc, bool* fail, cd d11, cd d21) {
+  constexpr int UNR = NFIX ? NC : 1;
+  const int n = NFIX ? NFIX : n_rt;
+  const cd* r1 = S + (size_t)lab[0] * L;
+  const cd* r2 = S + (size_t)lab[1] * L;
+  cd d12 = make_double2(0.0, 0.0), d22 = d12;
+  int e1 = -4096, e2 = -4096;
+#pragma unroll UNR
+  for (int q = 0; q < n; q++) {
+    const int c = colp[q];
+    const cd b1 = ldS(r1 + c), b2 = ldS(r2 + c);
+    const cd z2 = Y[(n + q) * ys];
+    e1 = max(e1, expo(b1));
+    e2 = max(e2, expo(b2));
+    d12 = cfma(b1, z2, d12);
+    d22 = cfma(b2, z2, d22);
+  }
+  const cd dd = cfms(d12, d21, cmul(d11, d22));
+  const cd d = cmul(Y[2 * n * ys], dd);
+  *fail = expo(d) < e1 + e2 + ey - kc;
+  return d;
+}
+
+// Row-difference update of a one-row member whose lemma guard failed.  Adding a multiple of
+// one row of a matrix to another leaves its determinant unchanged, so for any shared row a_r
+//   det [A; b] = det [A; b - a_r] = (b - a_r) . y      (y: the member row's cofactors, A y = 0).
+// A member that is near-singular because its row b nearly repeats a shared row (two labels
+// whose propagator rows almost coincide) loses its determinant to cancellation in b . y; the
+// rounded difference b - a_r is the small remainder itself, correct to one rounding per
+// entry (a floating-point subtraction rounds the exact difference once), so its dot with y
+// does not cancel.  a_r: the shared row nearest to b in the sink's first column (|re| + |im|
+// of the difference, lowest row on ties).  The lemma guard is taken again on the difference
+// row; when it fails too the caller refactors.  Off the hot path (one call per failed pair),
+// so not inlined.
+static __device__ __noinline__ cd rowdiff_det(const cd* __restrict__ S, int L, int n, int32_t blab,
+                                       const int32_t* __restrict__ arow,
+                                       const int32_t* __restrict__ colp, const cd* __restrict__ Y,
+                                       int ys, int ey, int kc, bool* fail) {
+  const cd* rb = S + (size_t)blab * L;
+  const int c0 = colp[0];
+  const cd b0 = ldS(rb + c0);
+  int r = 0;
+  double best = -1.0;
+  for (int i = 0; i < n - 1; i++) {
+    const cd x = ldS(S + (size_t)arow[i] * L + c0);
+    const double v = abs1(make_double2(b0.x - x.x, b0.y - x.y));
+    if (best < 0.0 || v < best) {
+      best = v;
+      r = i;
+    }
+  }
+  const cd* ra = S + (size_t)arow[r] * L;
+  cd d = make_double2(0.0, 0.0);
+  int eb = -4096;
+  for (int q = 0; q < n; q++) {
+    const int c = colp[q];
+    const cd x = ldS(rb + c), z = ldS(ra + c);
+    const cd del = make_double2(x.x - z.x, x.y - z.y);
+    eb = max(eb, expo(del));
+    d = cfma(del, Y[q * ys], d);
+  }
+  *fail = expo(d) < eb + ey - kc;
+  return d;
+}
+
+// Flops of one rowdiff_det call (planner's rule): the search (a complex difference and
+// |re| + |im| per shared row), the differences and the dot.
+__host__ __device__ constexpr int rowdiff_flops(int n) { return 3 * (n - 1) + 10 * n; }
+
 // Two-sided update: the sink belongs to a sink family whose members share every column but
 // the last, so G = [[B, a], [g^T, alpha]] with B the block of shared rows and shared
 // columns.  By the Schur complement det G = alpha det B - g^T adj(B) a, i.e. det G = g' . y

@@ -45,7 +45,8 @@ __global__ void combine_cw(const double* __restrict__ t, double* __restrict__ ou
 size_t forward_smem_bytes(int slots, int tile) {
   const size_t cache = (size_t)slots * tile * sizeof(double2);
   const size_t queue = (size_t)(tile / 32) * kQueueCap * kQueueEntryBytes;
-  return cache + queue;
+  const size_t z1 = (size_t)(tile / 32) * kZ1Bytes;
+  return cache + queue + z1;
 }
 
 // fwd_kernel over items [0, items): one launch per layout range, each with its own y

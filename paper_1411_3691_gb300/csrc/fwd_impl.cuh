@@ -21,7 +21,7 @@ struct QEntry {
   int32_t member;  // member slot
   int32_t lane;    // lane (sink) of the warp that produced it
   int32_t fail;    // flavours to refactor (bit f)
-  int32_t pad;
+  int32_t pguard;  // of those, the flavours whose shared rows failed the pivot guard
   double2 prod;    // product of the flavours that did not fail
   double w;        // signed w_i w_j of the pair
   double pad2;
@@ -94,24 +94,20 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
 #pragma unroll
   for (int k = 0; k < NR; k++) {
     if (k >= M) break;
-    // pivot: the largest |re| + |im| in column k among the unused rows, lowest row on ties
+    // pivot: the largest |re| + |im| in column k among the unused rows, by one warp-wide
+    // maximum of a key made of the measure's sign, exponent and leading 15 mantissa bits
+    // with (31 - lane) below them: a pivot within 2^-15 of the largest, the lowest row of
+    // those -- partial pivoting up to that tie tolerance; a zero measure keeps key bits 5..31
+    // zero, which is how an exactly zero pivot column shows
     const bool cand = lane < n && !((piv >> lane) & 1);
-    double best = cand ? dev::abs1(R[k]) : -1.0;
-    int idx = cand ? lane : 64;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(FULL, best, o);
-      const int oi = __shfl_xor_sync(FULL, idx, o);
-      const bool take = ob > best || (ob == best && oi < idx);
-      best = take ? ob : best;
-      idx = take ? oi : idx;
-    }
-    const int p = idx;
+    const unsigned mkey = cand ? (((unsigned)__double2hiint(dev::abs1(R[k])) & ~31u) | (unsigned)(31 - lane)) : 0u;
+    const unsigned top = __reduce_max_sync(FULL, mkey);
+    const int p = 31 - (int)(top & 31u);
     // the permutation's parity: p moves ahead of the unused rows that precede it
     parity ^= __popc(~piv & ((1u << p) - 1u) & ((1u << n) - 1u)) & 1;
     piv |= 1u << p;
     mystep = lane == p ? k : mystep;
-    zero |= best == 0.0;
+    zero |= (top >> 5) == 0u;
     const dev::cd pk = make_double2(__shfl_sync(FULL, R[k].x, p), __shfl_sync(FULL, R[k].y, p));
     det = (k == 0) ? pk : dev::cmul(det, pk);
     const dev::cd rc = dev::crcp(pk);
@@ -198,15 +194,41 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
 // one per lane.  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& e, int64_t j,
-                              double2& acc, unsigned long long& rflops) {
+                              const double2* Yw, double2& acc, unsigned long long& rflops,
+                              unsigned long long& nrd) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const int T = blockDim.x;
   const int32_t* cols = dev::sink_cols(a, j);
   double2 prod = have ? e.prod : make_double2(1.0, 0.0);
+  int32_t fail = have ? e.fail : 0;
   const int Q = a.snk_orig ? a.snk_q[j] : -1;
+  if (a.rowdiff && have) {
+    // one-row members that failed the lemma guard (not the pivot guard): the row-difference
+    // update with the cached solve of the pair's sink (lane e.lane of this warp), whose scale
+    // exponent is the largest of its n entries
+    const unsigned cand = (unsigned)(e.fail & ~e.pguard);
+    for (int f = 0; f < a.F; f++) {
+      const int n = a.n_f[f];
+      if (!((cand >> f) & 1) || n < 2 || a.fam_rank[(int64_t)W * a.F + f] != 1) continue;
+      const double2* Yf = Yw + (size_t)a.yoff[f] * T + e.lane;
+      int ey = -4096;
+      for (int q = 0; q < n; q++) ey = max(ey, dev::expo(Yf[q * T]));
+      bool f2 = true;
+      const int32_t* mlab = a.mem_lab + ((int64_t)e.member * a.F + f) * MHC_MAX_RANK;
+      const double2 d = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
+                                         cols + a.off_f[f], Yf, T, ey, a.kc, &f2);
+      rflops += dev::rowdiff_flops(n);
+      if (!f2) {
+        prod = dev::cmul(prod, d);
+        fail &= ~(1 << f);
+        nrd++;
+      }
+    }
+  }
   int32_t rows[NCMAX];
   for (int f = 0; f < a.F; f++) {
-    const bool need = have && ((e.fail >> f) & 1);
+    const bool need = have && ((fail >> f) & 1);
     const int n = a.n_f[f];
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
     const int sig = (Q >= 0 && a.q_two[Q]) ? a.q_rank[(int64_t)Q * a.F + f] : 0;
@@ -243,12 +265,13 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
 // Refactor the first count queued pairs (one per lane).  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
-                              double2& acc, unsigned long long& rflops) {
+                              const double2* Yw, double2& acc, unsigned long long& rflops,
+                              unsigned long long& nrd) {
   const int lane = threadIdx.x & 31;
   const bool have = lane < count;
   QEntry e = {};
   if (have) e = q[lane];
-  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), acc, rflops);
+  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), Yw, acc, rflops, nrd);
 }
 
 // One work item (family W x sink tile) by the whole thread block; the block's sum goes
@@ -267,13 +290,14 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
   QEntry* queue = reinterpret_cast<QEntry*>(smem + (size_t)a.slots * T) + warp * kQueueCap;
   double2* Y = smem + tid;
+  const double2* Yw = smem + (tid & ~31);  // the warp's cached solves (lane l: Yw + l)
 
   // ---- per flavour: factorise the shared rows against this sink ----------------------
   unsigned pguard = 0;
-  int ey[MHC_FMAX];
+  dev::FlavourScales eys;
   for (int f = 0; f < a.F; f++) {
     const int n = a.n_f[f];
-    ey[f] = 0;
+    int ey = 0;
     if (n == 0) continue;
     const int rho = a.fam_rank[(int64_t)W * a.F + f];
     const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
@@ -283,21 +307,56 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       const double2* K = a.kbuf + ((int64_t)W * a.n_q + Q) * a.kstride + a.koff[f];
       if (rho == 2 && sig == 2)
         dev::dispatch_kapply22<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                      Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+                                      Y + (size_t)a.yoff[f] * T, T, &ey);
       else if (rho == 2)
         dev::dispatch_kapply2<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                     Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+                                     Y + (size_t)a.yoff[f] * T, T, &ey);
       else if (sig == 2)
         dev::dispatch_kapply12<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                      Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+                                      Y + (size_t)a.yoff[f] * T, T, &ey);
       else
         dev::dispatch_kapply<NCMAX>(n, a.S[f], a.L_f[f], arow, cols + a.off_f[f], K,
-                                    Y + (size_t)a.yoff[f] * T, T, &ey[f]);
+                                    Y + (size_t)a.yoff[f] * T, T, &ey);
     } else {
       const bool g = dev::dispatch_shared<NCMAX>(n, rho, a.S[f], a.L_f[f], arow, cols + a.off_f[f],
-                                                 Y + (size_t)a.yoff[f] * T, T, &ey[f], a.kp);
+                                                 Y + (size_t)a.yoff[f] * T, T, &ey, a.kp);
       pguard |= (unsigned)g << f;
     }
+    eys.set(f, ey);
+  }
+
+  // ---- rank-2 flavours against a one-column sink family shared by the warp's sinks: the
+  // members' dots with the block's first null vector, once per warp (lane t: member t) -----
+  // (two-row families need n_f >= 10: the classes below compile none of this)
+  constexpr bool kZ1 = NCMAX >= 10;
+  int zf0 = -1, zf1 = -1;
+  double2* z1d = reinterpret_cast<double2*>(reinterpret_cast<char*>(smem + (size_t)a.slots * T) +
+                                            (size_t)(T >> 5) * kQueueCap * kQueueEntryBytes +
+                                            (size_t)warp * kZ1Bytes);
+  // (the shuffle and the vote run on every lane: qtwo differs between lanes whose sinks
+  // belong to a two-sided family and lanes whose sinks stand alone)
+  const int Q0 = kZ1 ? __shfl_sync(0xffffffffu, Q, 0) : 0;
+  const bool z1_warp = kZ1 && __all_sync(0xffffffffu, qtwo && Q == Q0);
+  if (kZ1 && z1_warp && kW <= 32) {
+    // the flavours are chosen from warp-uniform data only (W, Q), so every lane assigns the
+    // same slots; such a flavour took kapply2 on every lane
+    for (int f = 0; f < a.F && zf1 < 0; f++) {
+      const int n = a.n_f[f];
+      if (n == 0 || a.fam_rank[(int64_t)W * a.F + f] != 2 || a.q_rank[(int64_t)Q * a.F + f] != 1 ||
+          a.kguard[((int64_t)W * a.n_q + Q) * a.F + f])
+        continue;
+      const int slot = zf0 < 0 ? 0 : 1;
+      if (lane < kW) {
+        double2 d11, d21;
+        dev::dispatch_dots_z1<NCMAX>(n, a.S[f], a.L_f[f],
+                                     a.mem_lab + ((int64_t)(mem0 + lane) * a.F + f) * MHC_MAX_RANK,
+                                     cols + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, &d11, &d21);
+        z1d[(slot * 32 + lane) * 2] = d11;
+        z1d[(slot * 32 + lane) * 2 + 1] = d21;
+      }
+      if (slot == 0) zf0 = f; else zf1 = f;
+    }
+    __syncwarp();
   }
 
   // ---- per member: one dot product per flavour --------------------------------------
@@ -307,7 +366,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   // end); accq: the refactored pairs, w_i w_j included (a queue lane holds other sinks' pairs)
   double2 acc = make_double2(0.0, 0.0), accq = make_double2(0.0, 0.0);
   int qn = 0;
-  unsigned long long n_parent = 0, n_child = 0, rflops = 0;
+  unsigned long long n_parent = 0, n_child = 0, n_rowdiff = 0, rflops = 0;
   for (int c = 0; c < kW; c++) {
     const int m = mem0 + c;
     unsigned fail = pguard;
@@ -318,9 +377,17 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       if (n == 0 || ((pguard >> f) & 1)) continue;
       const int rho = a.fam_rank[(int64_t)W * a.F + f];
       bool cf = false;
-      const double2 d = dev::dispatch_member<NCMAX>(
-          n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK,
-          cols + a.off_f[f], Y + (size_t)a.yoff[f] * T, T, ey[f], a.kc, &cf);
+      const int32_t* mlab = a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK;
+      const double2* Yf = Y + (size_t)a.yoff[f] * T;
+      double2 d;
+      if (kZ1 && (f == zf0 || f == zf1)) {
+        const double2* zd = z1d + ((f == zf0 ? 0 : 32) + c) * 2;
+        d = dev::dispatch_member_z1<NCMAX>(n, a.S[f], a.L_f[f], mlab, cols + a.off_f[f], Yf, T, eys.get(f),
+                                           a.kc, &cf, zd[0], zd[1]);
+      } else {
+        d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], mlab, cols + a.off_f[f], Yf, T, eys.get(f),
+                                        a.kc, &cf);
+      }
       if (cf) {
         fail |= 1u << f;
       } else {
@@ -344,11 +411,11 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       e.member = m;
       e.lane = lane;
       e.fail = (int32_t)fail;
-      e.pad = 0;
+      e.pguard = (int32_t)pguard;
       e.prod = prod;
       e.w = wi * wj;
       e.pad2 = 0.0;
-      process_pairs<NCMAX>(a, W, true, e, j, accq, rflops);
+      process_pairs<NCMAX>(a, W, true, e, j, Yw, accq, rflops, n_rowdiff);
       n_parent += __popc(fail & pguard);
       n_child += __popc(fail & ~pguard);
     } else if (ball) {
@@ -358,7 +425,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
         e.member = m;
         e.lane = lane;
         e.fail = (int32_t)fail;
-        e.pad = 0;
+        e.pguard = (int32_t)pguard;
         e.prod = prod;
         e.w = wi * wj;
         e.pad2 = 0.0;
@@ -369,7 +436,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       qn += __popc(ball);
       __syncwarp();
       if (qn >= 32) {
-        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, accq, rflops);
+        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, Yw, accq, rflops, n_rowdiff);
         __syncwarp();
         if (lane < qn - 32) queue[lane] = queue[32 + lane];
         __syncwarp();
@@ -377,7 +444,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       }
     }
   }
-  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, accq, rflops);
+  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, Yw, accq, rflops, n_rowdiff);
   acc.x = fma(wj, acc.x, accq.x);
   acc.y = fma(wj, acc.y, accq.y);
 
@@ -386,6 +453,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   for (int o = 16; o > 0; o >>= 1) {
     n_parent += __shfl_xor_sync(0xffffffffu, n_parent, o);
     n_child += __shfl_xor_sync(0xffffffffu, n_child, o);
+    n_rowdiff += __shfl_xor_sync(0xffffffffu, n_rowdiff, o);
     rflops += __shfl_xor_sync(0xffffffffu, rflops, o);
   }
   __syncthreads();
@@ -401,10 +469,11 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
     *partial = s;
     if (!dev::finite2(s)) atomicOr(&a.counters[0], kStatusNonFinite);
   }
-  if (lane == 0 && (n_parent | n_child)) {
+  if (lane == 0 && (n_parent | n_child | n_rowdiff)) {
     atomicAdd(&a.counters[1], n_parent);
-    atomicAdd(&a.counters[2], n_child);
-    atomicAdd(&a.counters[3], rflops);
+    atomicAdd(&a.counters[2], n_child - n_rowdiff);  // queued for the lemma guard, less those the
+    atomicAdd(&a.counters[3], rflops);               // row-difference update resolved
+    atomicAdd(&a.counters[4], n_rowdiff);
   }
 }
 
@@ -453,9 +522,18 @@ __global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pai
                                               a.fam_arow + (int64_t)W * a.Tn + a.off_f[f], col,
                                               Y, T, &ey, a.kp);
       if (!fail) {
-        d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f],
-                                        a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK, col, Y, T, ey,
-                                        a.kc, &fail);
+        const int32_t* mlab = a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK;
+        d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], mlab, col, Y, T, ey, a.kc, &fail);
+        if (fail && rho == 1 && n >= 2 && a.rowdiff) {
+          bool f2 = true;
+          const double2 d2 = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
+                                              col, Y, T, ey, a.kc, &f2);
+          if (!f2) {
+            d = d2;
+            fail = false;
+            bits |= 1 << (8 + f);
+          }
+        }
       }
       if (fail) {
         dev::member_rows(a, W, m, f, rho, rows);

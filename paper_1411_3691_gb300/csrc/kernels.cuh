@@ -22,6 +22,7 @@ enum : unsigned long long {
 // Everything one forward evaluation of one plan needs on the device.
 struct FwdArgs {
   int F, Tn, n_tiles, slots, kp, kc;
+  int rowdiff;               // 1: the row-difference update before a lemma-guard refactor
   int64_t n_snk;
   int n_f[MHC_FMAX], L_f[MHC_FMAX], off_f[MHC_FMAX], yoff[MHC_FMAX];
   const double2* S[MHC_FMAX];
@@ -143,6 +144,28 @@ __device__ __forceinline__ cd dispatch_member(int n, int rho, const cd* S, int L
 }
 
 template <int NCMAX>
+__device__ __forceinline__ void dispatch_dots_z1(int n, const cd* S, int L, const int32_t* lab,
+                                                 const int32_t* col, const cd* Y, int ys, cd* d11,
+                                                 cd* d21) {
+  if constexpr (NCMAX >= 18) {
+    if (n == 12) { member_dots_z1<12, 12>(S, L, 12, lab, col, Y, ys, d11, d21); return; }
+    if (n == 18) { member_dots_z1<18, 18>(S, L, 18, lab, col, Y, ys, d11, d21); return; }
+  }
+  member_dots_z1<NCMAX, 0>(S, L, n, lab, col, Y, ys, d11, d21);
+}
+
+template <int NCMAX>
+__device__ __forceinline__ cd dispatch_member_z1(int n, const cd* S, int L, const int32_t* lab,
+                                                 const int32_t* col, const cd* Y, int ys, int ey, int kc,
+                                                 bool* fail, cd d11, cd d21) {
+  if constexpr (NCMAX >= 18) {
+    if (n == 12) return member_det_z1<12, 12>(S, L, 12, lab, col, Y, ys, ey, kc, fail, d11, d21);
+    if (n == 18) return member_det_z1<18, 18>(S, L, 18, lab, col, Y, ys, ey, kc, fail, d11, d21);
+  }
+  return member_det_z1<NCMAX, 0>(S, L, n, lab, col, Y, ys, ey, kc, fail, d11, d21);
+}
+
+template <int NCMAX>
 __device__ __forceinline__ void dispatch_kapply(int n, const cd* S, int L, const int32_t* arow,
                                                 const int32_t* col, const cd* K, cd* Y, int ys,
                                                 int* ey) {
@@ -247,6 +270,22 @@ __device__ __forceinline__ void member_rows(const FwdArgs& a, int W, int m, int 
   for (int t = 0; t < rho; t++) rows[n - rho + t] = a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK + t];
 }
 
+// Per-flavour exponent scales of the member guard, packed 16 bits per flavour into two 64-bit
+// registers: an array indexed by the runtime flavour would live in local memory, and the
+// member loop reads it for every member and flavour.
+struct FlavourScales {
+  unsigned long long w[2] = {0ull, 0ull};
+  __device__ __forceinline__ void set(int f, int v) {
+    const int s = 16 * (f & 3);
+    const unsigned long long m = 0xffffull << s;
+    const unsigned long long x = (unsigned long long)(unsigned short)(short)v << s;
+    if (f < 4) w[0] = (w[0] & ~m) | x; else w[1] = (w[1] & ~m) | x;
+  }
+  __device__ __forceinline__ int get(int f) const {
+    return (int)(short)(unsigned short)(((f < 4) ? w[0] : w[1]) >> (16 * (f & 3)));
+  }
+};
+
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -272,6 +311,10 @@ struct BatchItem {
 // per-warp refactor queue of the forward kernel
 constexpr int kQueueCap = 64;         // entries per warp
 constexpr int kQueueEntryBytes = 48;  // sizeof(fwd::QEntry)
+// per-warp store of the members' dots with a block's first null vector (rank-2 families
+// against one-column sink families): two flavours, 32 members, two complex values
+constexpr int kZ1Flavours = 2;
+constexpr int kZ1Bytes = kZ1Flavours * 32 * 2 * 16;
 
 // host-side launchers (forward.cu and fwd_nc*.cu)
 cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,

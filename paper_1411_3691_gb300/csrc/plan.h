@@ -21,6 +21,10 @@ namespace mhc {
 
 void set_error(const std::string& msg);
 
+// device counters of a plan: status bits, refactor parent, refactor child, refactor flops,
+// row-difference updates
+constexpr int kNumCounters = 5;
+
 // Device-side tables of one plan (owned by the plan, allocated on first use).
 struct DevicePlan {
   int device = -1;
@@ -59,7 +63,8 @@ struct DevicePlan {
   double* w_src = nullptr;       // [n_src] plan weights
   double* w_snk = nullptr;       // [n_snk]
   double* partials = nullptr;    // [items][2] per-work-item partial sums
-  unsigned long long* counters = nullptr;  // [4]: status bits, refactor parent, child, refactor flops
+  unsigned long long* counters = nullptr;  // [kNumCounters]: status bits, refactor parent, child,
+                                           // refactor flops, row-difference updates
   int64_t n_items = 0;
   int32_t n_tiles = 0;           // sink tiles per family
   int32_t tile = 0;              // sinks per tile (threads per block)

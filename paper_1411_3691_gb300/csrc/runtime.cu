@@ -192,8 +192,8 @@ mhc_status ensure_device(Plan& p) {
   d.n_tiles = (int32_t)((p.n_snk + d.tile - 1) / d.tile);
   d.n_items = p.n_fam * d.n_tiles;
   if ((st = upload<double>(&d.partials, nullptr, 2 * (size_t)d.n_items)) != MHC_OK) return st;
-  if ((st = upload<unsigned long long>(&d.counters, nullptr, 4)) != MHC_OK) return st;
-  MHC_CUDA(cudaMemset(d.counters, 0, 4 * sizeof(unsigned long long)));
+  if ((st = upload<unsigned long long>(&d.counters, nullptr, kNumCounters)) != MHC_OK) return st;
+  MHC_CUDA(cudaMemset(d.counters, 0, kNumCounters * sizeof(unsigned long long)));
   (void)F;
   d.device = cur;
   return MHC_OK;
@@ -209,6 +209,7 @@ mhc_status fill_fwd_args(Plan& p, const double* const* S_f, const double* w_src,
   plan_slots(p, a.yoff, &a.slots);
   a.kp = log2_inv(p.opts.tau_parent);
   a.kc = log2_inv(p.opts.tau_child);
+  a.rowdiff = p.opts.row_difference ? 1 : 0;
   for (int f = 0; f < p.F; f++) {
     a.n_f[f] = p.n_f[f];
     a.L_f[f] = p.L_f[f];
@@ -346,7 +347,7 @@ mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream) {
   }
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (p.dev.device < 0) return MHC_OK;
-  unsigned long long c[4] = {0, 0, 0, 0};
+  unsigned long long c[kNumCounters] = {0, 0, 0, 0, 0};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   MHC_CUDA(cudaStreamSynchronize(s));
   MHC_CUDA(cudaMemcpy(c, p.dev.counters, sizeof(c), cudaMemcpyDeviceToHost));
@@ -354,6 +355,7 @@ mhc_status mhc_get_status(mhc_plan_t plan, mhc_stream_t stream) {
   p.stats.refactor_parent = (int64_t)c[1];
   p.stats.refactor_child = (int64_t)c[2];
   p.stats.refactor_flops = (double)c[3];
+  p.stats.row_difference = (int64_t)c[4];
   if (c[0] & kStatusTimeout) {
     set_error("a bounded device wait ran out");
     return MHC_ETIMEOUT;

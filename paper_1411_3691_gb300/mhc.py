@@ -46,7 +46,7 @@ class PlanOpts(ctypes.Structure):
                 ("sink_tile", ctypes.c_int32), ("rank2", ctypes.c_int32),
                 ("max_family", ctypes.c_int32), ("one_sided", ctypes.c_int32),
                 ("rank3", ctypes.c_int32), ("max_rank", ctypes.c_int32), ("first_fit", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("row_difference", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("refactor_child", ctypes.c_int64), ("sink_families", ctypes.c_int64),
                 ("two_sided_blocks", ctypes.c_int64), ("backward_flops_per_call", ctypes.c_double),
                 ("rank3_family_flavours", ctypes.c_int64), ("refactor_flops", ctypes.c_double),
-                ("rank4plus_family_flavours", ctypes.c_int64)]
+                ("rank4plus_family_flavours", ctypes.c_int64), ("row_difference", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -108,27 +108,46 @@ def test_weights_override(M):
     assert abs(C - ref) <= 1e-11 * scale
 
 
-def test_pair_dets(M):
+@pytest.mark.parametrize("row_difference", [0, 1])
+def test_pair_dets(M, row_difference):
+    """Every pair of the forced workload through the probe against the oracle.  The forced
+    near-singular members (a changed row set to the near-twin of a shared row) left the
+    lemma update for every sink: by a refactor (default), or with row_difference = 1 by the
+    row-difference update (one-row families) or a refactor (two-row families)."""
     w = CASES["large_rank2_forced"]
-    plan = M.Plan.from_workload(w)
+    opts = M.default_opts()
+    opts.row_difference = row_difference
+    plan = M.Plan.from_workload(w, opts)
     S = dev_S(w)
     ii, jj = np.meshgrid(np.arange(len(w.w_src)), np.arange(len(w.w_snk)), indexing="ij")
     path, n_ill = check_pairs(M, w, plan, S, ii.ravel(), jj.ravel())
-    # the forced near-singular members took the refactor path for every sink
     forced = w.meta["src"]["forced"]
     assert len(forced) > 0
     P = path.reshape(len(w.w_src), len(w.w_snk))
     for t, f in forced:
-        assert np.all((P[t] >> f) & 1), (t, f)
+        assert np.all(((P[t] >> f) | (P[t] >> (8 + f))) & 1), (t, f)
+    if row_difference:
+        assert np.any(P >> 8)  # some forced members were one-row members
+    else:
+        assert not np.any(P >> 8)
 
 
-def test_refactor_counters(M):
+@pytest.mark.parametrize("row_difference", [0, 1])
+def test_refactor_counters(M, row_difference):
     w = CASES["large_rank2_forced"]
-    C, plan, S = gpu_C(M, w)
+    opts = M.default_opts()
+    opts.row_difference = row_difference
+    C, plan, S = gpu_C(M, w, opts)
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
     st = plan.stats()
     forced = w.meta["src"]["forced"]
-    assert st["refactor_child"] >= len(forced) * len(w.w_snk)
+    assert st["refactor_child"] + st["row_difference"] >= len(forced) * len(w.w_snk)
+    if row_difference:
+        assert st["row_difference"] > 0
+    else:
+        assert st["row_difference"] == 0
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
 
 
 def test_nonfinite_status(M):
@@ -148,14 +167,33 @@ def test_full_helium4(M):
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
 
 
-def test_full_large_nucleus_sampled(M):
+_LARGE = {}
+
+
+def _large_and_reference():
+    """The large nucleus, and the oracle's C over 32 random source families x all sinks
+    (computed once for the parametrised test below)."""
+    if not _LARGE:
+        w = wl.large_nucleus()
+        ws, keep = family_mask(w, 32, seed=33)
+        _LARGE.update(w=w, ws=ws, keep=keep, ref=oracle_subset(w, keep))
+    return _LARGE
+
+
+@pytest.mark.parametrize("row_difference", [0, 1])
+def test_full_large_nucleus_sampled(M, row_difference):
     """32768 x 32768, n = 18, in the plan and launch configuration the benchmark times:
     10^5 seeded pairs through the probe against the oracle (1e-12 relative, or the
-    conditioning bound for the forced near-singular members, which must have taken the
-    refactor path), and C of the full plan with the source weights of all but 32 random
-    families set to zero against the oracle's sum over those families x all 32768 sinks."""
-    w = wl.large_nucleus()
-    plan = M.Plan.from_workload(w)
+    conditioning bound for the forced near-singular members, which must have left the
+    lemma update: refactored, or with row_difference = 1 the one-row ones by the
+    row-difference update), and C of the full plan with the source weights of all but 32
+    random families set to zero against the oracle's sum over those families x all 32768
+    sinks."""
+    L = _large_and_reference()
+    w = L["w"]
+    opts = M.default_opts()
+    opts.row_difference = row_difference
+    plan = M.Plan.from_workload(w, opts)
     S = dev_S(w)
     rng = np.random.default_rng(31)
     ii = rng.integers(0, len(w.w_src), 100000)
@@ -165,14 +203,16 @@ def test_full_large_nucleus_sampled(M):
     for p in range(len(ii)):
         for f in range(2):
             if (int(ii[p]), f) in forced:
-                assert (path[p] >> f) & 1, (ii[p], jj[p], f)
-    ws, keep = family_mask(w, 32, seed=33)
+                assert ((path[p] >> f) | (path[p] >> (8 + f))) & 1, (ii[p], jj[p], f)
+    ws, keep = L["ws"], L["keep"]
     assert len(keep) == 32 * 32
     out = plan.correlator(S, torch.from_numpy(ws).cuda())
     C = complex(*out.cpu().numpy())
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
-    assert plan.stats()["refactor_child"] > 0          # the forced members were refactored
-    ref, scale = oracle_subset(w, keep)
+    st = plan.stats()
+    assert st["refactor_child"] > 0                    # refactored (two-row forced members at least)
+    assert (st["row_difference"] > 0) == bool(row_difference)
+    ref, scale = L["ref"]
     assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
     plan.close()
 
@@ -252,7 +292,8 @@ def test_forced_members_in_multi_row_families(M, three_row_frac):
     ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
     assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
-    assert plan.stats()["refactor_child"] >= len(forced) * len(w.w_snk) // 2
+    st = plan.stats()
+    assert st["refactor_child"] + st["row_difference"] >= len(forced) * len(w.w_snk) // 2
     plan.close()
 
 
@@ -315,4 +356,21 @@ def test_rank_k_families(M, k, one_sided):
     assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
     ii, jj = np.meshgrid(np.arange(len(w.w_src)), np.arange(len(w.w_snk)), indexing="ij")
     check_pairs(M, w, plan, S, ii.ravel(), jj.ravel())
+    plan.close()
+
+
+def test_two_row_sources_against_warp_wide_sink_families(M):
+    """Two-row source families against one-column sink families of exactly 32 sinks, so
+    that each warp's sinks share one sink family: the members' dots with the block's first
+    null vector are formed once per warp.  C against the oracle."""
+    a = wl.make_workload("r2w", [12, 10], [60, 48], [7, 5, 6, 9], [32, 32, 32], seed=48, two_row_frac=0.7)
+    b = wl.make_workload("r2w", [12, 10], [60, 48], [7, 5, 6, 9], [32, 32, 32], seed=48, two_row_frac=0.0)
+    assert all(np.array_equal(x, y) for x, y in zip(a.S, b.S))
+    w = wl.Workload("r2w", a.n_f, a.S, a.labels_src, a.w_src, b.labels_snk, b.w_snk)
+    C, plan, S = gpu_C(M, w)
+    assert plan.stats()["rank2_family_flavours"] > 0
+    assert np.all(plan.sinks()["two_sided"] == 1)
+    ref, scale = oracle.correlator(w.S, w.n_f, w.labels_src, w.w_src, w.labels_snk, w.w_snk, threads=8)
+    assert abs(C - ref) <= 1e-11 * scale, (C, ref, abs(C - ref) / scale)
+    assert M.mhc_get_status_code(plan.handle) == M.MHC_OK
     plan.close()
