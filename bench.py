@@ -53,10 +53,11 @@ NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # + 99.5 MB written per call of the copy (kfac_kernel, kfac_group_kernel, three fwd_kernel
 # launches, reduce_kernel).
 TRAFFIC = {
-    "large": {"bytes": 265.40e6 * 64,
-              "source": "ncu dram bytes of every kernel of one call of the 1/8-per-side copy "
-                        "(--workload large_small), x 64"},
-    "he4": {"bytes": 69.93e6, "source": "ncu dram bytes of the fwd_kernel launch of one call"},
+    "large": {"bytes": 269.76e6 * 64,
+              "source": "ncu dram__bytes_read + dram__bytes_write of every kernel of one call of the "
+                        "1/8-per-side copy (--workload large_small), x 64"},
+    "he4": {"bytes": 108.87e6,
+            "source": "ncu dram__bytes_read + dram__bytes_write of every kernel of one call"},
 }
 
 
@@ -412,7 +413,7 @@ def run_gpu(args):
         }
 
     if rank == 0:
-        traffic = TRAFFIC.get(args.workload)
+        traffic = None if args.row_difference else TRAFFIC.get(args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

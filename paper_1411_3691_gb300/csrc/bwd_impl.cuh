@@ -1025,7 +1025,7 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
 
     // ---- pass 1: cached solves, member dets (fresh where guarded), dw partials --------
     unsigned pguard = 0;
-    dev::FlavourScales eys;
+    dev::ScalesFor<NCMAX> eys;
     for (int f = 0; f < a.F; f++) {
       const int n = a.n_f[f];
       int ey = 0;

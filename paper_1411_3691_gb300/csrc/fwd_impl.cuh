@@ -294,7 +294,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
 
   // ---- per flavour: factorise the shared rows against this sink ----------------------
   unsigned pguard = 0;
-  dev::FlavourScales eys;
+  dev::ScalesFor<NCMAX> eys;
   for (int f = 0; f < a.F; f++) {
     const int n = a.n_f[f];
     int ey = 0;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/mhc.h"
 #include "device.cuh"
 #include "layout.h"
@@ -272,7 +274,13 @@ __device__ __forceinline__ void member_rows(const FwdArgs& a, int W, int m, int 
 
 // Per-flavour exponent scales of the member guard, packed 16 bits per flavour into two 64-bit
 // registers: an array indexed by the runtime flavour would live in local memory, and the
-// member loop reads it for every member and flavour.
+// member loop reads it for every member and flavour.  (The n <= 8 class keeps the array:
+// measured faster there -- its member dots are short and its loads hit L1.)
+struct FlavourScalesArray {
+  int e[MHC_FMAX];
+  __device__ __forceinline__ void set(int f, int v) { e[f] = v; }
+  __device__ __forceinline__ int get(int f) const { return e[f]; }
+};
 struct FlavourScales {
   unsigned long long w[2] = {0ull, 0ull};
   __device__ __forceinline__ void set(int f, int v) {
@@ -285,6 +293,8 @@ struct FlavourScales {
     return (int)(short)(unsigned short)(((f < 4) ? w[0] : w[1]) >> (16 * (f & 3)));
   }
 };
+template <int NCMAX>
+using ScalesFor = typename std::conditional<(NCMAX > 8), FlavourScales, FlavourScalesArray>::type;
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
