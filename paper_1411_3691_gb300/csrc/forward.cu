@@ -46,7 +46,8 @@ size_t forward_smem_bytes(int slots, int tile) {
   const size_t cache = (size_t)slots * tile * sizeof(double2);
   const size_t queue = (size_t)(tile / 32) * kQueueCap * kQueueEntryBytes;
   const size_t z1 = (size_t)(tile / 32) * kZ1Bytes;
-  return cache + queue + z1;
+  const size_t walk = (size_t)(tile / 32) * kWalkBytes;
+  return cache + queue + z1 + walk;
 }
 
 // fwd_kernel over items [0, items): one launch per layout range, each with its own y

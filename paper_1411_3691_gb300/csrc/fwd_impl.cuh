@@ -68,7 +68,7 @@ __device__ __forceinline__ unsigned long long group_pair_flops(int n, int rc) {
 // rule.  Called by the whole warp; returns the determinant on the lanes in grp.
 template <int NC, int RC>
 __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, int rho, int m, int Q,
-                                               int64_t j, unsigned grp) {
+                                               int64_t j, unsigned grp, dev::cd* wk) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int NR = NC - RC > 0 ? NC - RC : 1;
   const int lane = threadIdx.x & 31;
@@ -126,21 +126,48 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
   int left[RC];
   left[0] = __ffs(rest) - 1;
   if (RC == 2) left[RC - 1] = __ffs(rest & ~(1u << left[0])) - 1;
-  // V: lane i holds the coefficient of row i in each remaining row's functional
+  // V: lane i holds the coefficient of row i in each remaining row's functional.  In the
+  // order of the steps (position s < M: the pivot row of step s; M + t: the t-th remaining
+  // row), the functional's coefficient at position s is minus the sum, over the later
+  // positions s', of the multiplier of row s' at step s times the coefficient at s' -- a
+  // back substitution with the unit lower factor.  The multipliers are staged by step in
+  // the warp's shared scratch wk (column s: positions s + 1 .. n - 1, packed), and the
+  // substitution runs as pushes: once position s' is final it is broadcast and every
+  // earlier position adds its term, so the dependency chain per position is one shuffle and
+  // one complex multiply-add.
+  const int pos = mystep < NC ? mystep : (lane == left[0] ? M : M + RC - 1);
+  auto woff = [&](int c) { return c * (n - 1) - c * (c - 1) / 2; };  // column c of the packed store
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < NR; k++) {
+    if (k >= M) break;
+    if (lane < n && k < pos) wk[woff(k) + pos - k - 1] = R[k];  // this row's multiplier at step k
+  }
+  __syncwarp();
+  dev::cd acc[RC];
+#pragma unroll
+  for (int t = 0; t < RC; t++)  // the remaining rows: coefficient 1 in their own functional
+    acc[t] = lane < M ? wk[woff(lane) + M + t - lane - 1] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int sp = NR - 1; sp >= 1; sp--) {
+    if (sp >= M) continue;
+    dev::cd v[RC];
+#pragma unroll
+    for (int t = 0; t < RC; t++)
+      v[t] = dev::cneg(make_double2(__shfl_sync(FULL, acc[t].x, sp), __shfl_sync(FULL, acc[t].y, sp)));
+    if (lane < sp) {
+      const dev::cd w = wk[woff(lane) + sp - lane - 1];
+#pragma unroll
+      for (int t = 0; t < RC; t++) acc[t] = dev::cfma(w, v[t], acc[t]);
+    }
+  }
+  // back to row order: row i takes the coefficient of its position
+  const int src = pos < M ? pos : 0;
   dev::cd V[RC];
 #pragma unroll
-  for (int t = 0; t < RC; t++) V[t] = make_double2(lane == left[t] ? 1.0 : 0.0, 0.0);
-#pragma unroll
-  for (int k = NR - 1; k >= 0; k--) {
-    if (k >= M) continue;
-    const int p = __ffs(__ballot_sync(FULL, mystep == k)) - 1;
-    const bool unused = lane < n && mystep > k;
-#pragma unroll
-    for (int t = 0; t < RC; t++) {
-      double2 sum = unused ? dev::cmul(R[k], V[t]) : make_double2(0.0, 0.0);
-      sum = dev::warp_sum(sum);
-      if (lane == p) V[t] = dev::cneg(sum);
-    }
+  for (int t = 0; t < RC; t++) {
+    const dev::cd x = make_double2(-__shfl_sync(FULL, acc[t].x, src), -__shfl_sync(FULL, acc[t].y, src));
+    V[t] = lane >= n ? make_double2(0.0, 0.0) : pos < M ? x : make_double2(pos == M + t ? 1.0 : 0.0, 0.0);
   }
   // each lane: its sink's last RC columns against the RC functionals
   const bool mine = (grp >> lane) & 1;
@@ -194,7 +221,7 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
 // one per lane.  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& e, int64_t j,
-                              const double2* Yw, double2& acc, unsigned long long& rflops,
+                              const double2* Yw, double2* wk, double2& acc, unsigned long long& rflops,
                               unsigned long long& nrd) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -241,8 +268,8 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
       const int lq = __shfl_sync(FULL, Q, leader);
       const int lsig = __shfl_sync(FULL, sig, leader);
       const unsigned grp = __ballot_sync(FULL, ((todo >> lane) & 1) && e.member == lm && Q == lq);
-      const double2 d = lsig == 1 ? group_fresh<NCMAX <= 18 ? NCMAX : 18, 1>(a, W, f, rho, lm, lq, j, grp)
-                                  : group_fresh<NCMAX <= 18 ? NCMAX : 18, 2>(a, W, f, rho, lm, lq, j, grp);
+      const double2 d = lsig == 1 ? group_fresh<NCMAX <= 18 ? NCMAX : 18, 1>(a, W, f, rho, lm, lq, j, grp, wk)
+                                  : group_fresh<NCMAX <= 18 ? NCMAX : 18, 2>(a, W, f, rho, lm, lq, j, grp, wk);
       if ((grp >> lane) & 1) {
         prod = dev::cmul(prod, d);
         rflops += group_pair_flops(n, lsig) + (lane == leader ? group_shared_flops(n, lsig) : 0ull);
@@ -265,13 +292,13 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
 // Refactor the first count queued pairs (one per lane).  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_queue(const FwdArgs& a, int W, QEntry* q, int count, int64_t jbase,
-                              const double2* Yw, double2& acc, unsigned long long& rflops,
+                              const double2* Yw, double2* wk, double2& acc, unsigned long long& rflops,
                               unsigned long long& nrd) {
   const int lane = threadIdx.x & 31;
   const bool have = lane < count;
   QEntry e = {};
   if (have) e = q[lane];
-  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), Yw, acc, rflops, nrd);
+  process_pairs<NCMAX>(a, W, have, e, jbase + (have ? e.lane : 0), Yw, wk, acc, rflops, nrd);
 }
 
 // One work item (family W x sink tile) by the whole thread block; the block's sum goes
@@ -333,6 +360,10 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
   double2* z1d = reinterpret_cast<double2*>(reinterpret_cast<char*>(smem + (size_t)a.slots * T) +
                                             (size_t)(T >> 5) * kQueueCap * kQueueEntryBytes +
                                             (size_t)warp * kZ1Bytes);
+  // the warp's scratch for the grouped refactors' multipliers (group_fresh)
+  double2* wk = reinterpret_cast<double2*>(reinterpret_cast<char*>(smem + (size_t)a.slots * T) +
+                                           (size_t)(T >> 5) * (kQueueCap * kQueueEntryBytes + kZ1Bytes) +
+                                           (size_t)warp * kWalkBytes);
   // (the shuffle and the vote run on every lane: qtwo differs between lanes whose sinks
   // belong to a two-sided family and lanes whose sinks stand alone)
   const int Q0 = kZ1 ? __shfl_sync(0xffffffffu, Q, 0) : 0;
@@ -415,7 +446,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       e.prod = prod;
       e.w = wi * wj;
       e.pad2 = 0.0;
-      process_pairs<NCMAX>(a, W, true, e, j, Yw, accq, rflops, n_rowdiff);
+      process_pairs<NCMAX>(a, W, true, e, j, Yw, wk, accq, rflops, n_rowdiff);
       n_parent += __popc(fail & pguard);
       n_child += __popc(fail & ~pguard);
     } else if (ball) {
@@ -436,7 +467,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       qn += __popc(ball);
       __syncwarp();
       if (qn >= 32) {
-        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, Yw, accq, rflops, n_rowdiff);
+        process_queue<NCMAX>(a, W, queue, 32, (int64_t)tile * T + warp * 32, Yw, wk, accq, rflops, n_rowdiff);
         __syncwarp();
         if (lane < qn - 32) queue[lane] = queue[32 + lane];
         __syncwarp();
@@ -444,7 +475,7 @@ __device__ __forceinline__ void fwd_item(const FwdArgs& a, int W, int tile, doub
       }
     }
   }
-  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, Yw, accq, rflops, n_rowdiff);
+  if (qn > 0) process_queue<NCMAX>(a, W, queue, qn, (int64_t)tile * T + warp * 32, Yw, wk, accq, rflops, n_rowdiff);
   acc.x = fma(wj, acc.x, accq.x);
   acc.y = fma(wj, acc.y, accq.y);
 
@@ -746,9 +777,9 @@ cudaError_t launch_kfac_nc(const FwdArgs& a, int64_t n_fam, cudaStream_t s) {
 
 // Persistent batched launch: blocks pull (correlator, family, tile) items from a list
 // ordered by decreasing cost through one atomic counter; each item's partial goes to its
-// own slot (see batch.cu).
+// own slot (see batch.cu).  Registers as fwd_kernel's (at most 128 threads per block).
 template <int NCMAX>
-__global__ void __launch_bounds__(128) batch_kernel(const FwdArgs* __restrict__ desc,
+__global__ void __maxnreg__(NCMAX <= 8 ? 168 : 255) batch_kernel(const FwdArgs* __restrict__ desc,
                                                     const BatchItem* __restrict__ items,
                                                     int64_t n_items, unsigned long long* head,
                                                     const int64_t* __restrict__ part_off,

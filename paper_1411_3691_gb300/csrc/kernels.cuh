@@ -325,6 +325,10 @@ constexpr int kQueueEntryBytes = 48;  // sizeof(fwd::QEntry)
 // against one-column sink families): two flavours, 32 members, two complex values
 constexpr int kZ1Flavours = 2;
 constexpr int kZ1Bytes = kZ1Flavours * 32 * 2 * 16;
+// per-warp scratch of the grouped refactors: the multipliers of the shared elimination by
+// step, packed (n - 1 + n - 2 + ... + 1 complex values for n <= 18)
+constexpr int kWalkMaxN = 18;
+constexpr int kWalkBytes = kWalkMaxN * (kWalkMaxN - 1) / 2 * 16;
 
 // host-side launchers (forward.cu and fwd_nc*.cu)
 cudaError_t launch_forward(const FwdArgs& a, int ncmax, int tile, int64_t n_fam, int64_t items,

@@ -745,6 +745,41 @@ mhc_status build_plan(Plan& p) {
   // from the recomputed shared-row LU with the columns of A1^{-1} otherwise; per pair the
   // scatter and the weight gradients
   double bfl = fl;  // the forward part (without the final combine, added below)
+  // The forward's two-row members against one-column sink families: a warp whose 32 sinks
+  // all belong to one such family forms each member's dots with the block's first null
+  // vector once (they do not depend on the sink), for the first two such flavours of the
+  // family; per sink the member then needs the two dots with the second null vector.  The
+  // adjoint forms every dot per sink, so only the forward's count changes.
+  if (!p.snk_q.empty() && p.n_qfam > 0) {
+    std::vector<int64_t> zw(p.n_qfam, 0), zs(p.n_qfam, 0);  // such warps per sink family, their sinks
+    for (int64_t w0 = 0; w0 < p.n_snk; w0 += 32) {
+      const int64_t w1 = std::min<int64_t>(w0 + 32, p.n_snk);
+      const int32_t Q = p.snk_q[w0];
+      if (Q < 0 || !p.q_two[Q] || p.snk_q[w1 - 1] != Q) continue;
+      zw[Q]++;
+      zs[Q] += w1 - w0;
+    }
+    double save = 0.0;
+    for (int64_t W = 0; W < p.n_fam; W++) {
+      bool any2 = false;
+      for (int f = 0; f < F; f++) any2 |= p.fam_rank[W * F + f] == 2 && p.n_f[f] > 0;
+      if (!any2) continue;
+      const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
+      if (k > 32) continue;
+      for (int64_t Q = 0; Q < p.n_qfam; Q++) {
+        if (zw[Q] == 0) continue;
+        int used = 0;
+        for (int f = 0; f < F && used < 2; f++) {
+          const int n = p.n_f[f];
+          if (n == 0 || p.fam_rank[W * F + f] != 2 || p.q_rank[Q * F + f] != 1) continue;
+          const double dot = 6.0 + 8.0 * (n - 1);
+          save += k * (2.0 * dot * (double)zs[Q] - 2.0 * dot * (double)zw[Q]);
+          used++;
+        }
+      }
+    }
+    fl -= save;
+  }
   for (int64_t W = 0; W < p.n_fam; W++) {
     const double k = (double)(p.fam_off[W + 1] - p.fam_off[W]);
     for (int f = 0; f < F; f++) {
