@@ -52,6 +52,39 @@ __device__ __forceinline__ unsigned long long group_pair_flops(int n, int rc) {
   return (unsigned long long)(rc * rc * (8LL * n - 2) + (rc == 2 ? 2 + 6 + 6 + 8 + 12 : 6));
 }
 
+// Pivot search of one step of group_fresh: the largest |re| + |im| in column k (rk: this
+// lane's entry) among the unused rows, by one warp-wide maximum of a key made of the
+// measure's sign, exponent and leading 15 mantissa bits with (31 - lane) below them: a pivot
+// within 2^-15 of the largest, the lowest row of those -- partial pivoting up to that tie
+// tolerance; a zero measure keeps key bits 5..31 zero, which is how an exactly zero pivot
+// column shows.  Updates the used rows, the permutation's parity, the determinant and the
+// pivot's reciprocal.  Called by the whole warp.
+struct PivotState {
+  unsigned piv;  // rows already used as pivots
+  int mystep;    // the step at which this lane's row became the pivot (NC: never)
+  int parity;
+  bool zero;
+  dev::cd det;
+  int p;         // this step's pivot row
+  dev::cd rc;    // its reciprocal
+};
+__device__ __forceinline__ void select_pivot(PivotState& s, dev::cd rk, int k, int n, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const bool cand = lane < n && !((s.piv >> lane) & 1);
+  const unsigned mkey = cand ? (((unsigned)__double2hiint(dev::abs1(rk)) & ~31u) | (unsigned)(31 - lane)) : 0u;
+  const unsigned top = __reduce_max_sync(FULL, mkey);
+  const int p = 31 - (int)(top & 31u);
+  // the permutation's parity: p moves ahead of the unused rows that precede it
+  s.parity ^= __popc(~s.piv & ((1u << p) - 1u) & ((1u << n) - 1u)) & 1;
+  s.piv |= 1u << p;
+  s.mystep = lane == p ? k : s.mystep;
+  s.zero |= (top >> 5) == 0u;
+  const dev::cd pk = make_double2(__shfl_sync(FULL, rk.x, p), __shfl_sync(FULL, rk.y, p));
+  s.det = (k == 0) ? pk : dev::cmul(s.det, pk);
+  s.rc = dev::crcp(pk);
+  s.p = p;
+}
+
 // Fresh determinants of a group of queued pairs that share member m and a two-sided sink
 // family Q whose members change RC columns of flavour f (RC = 1 or 2; family of rank rho):
 // their matrices G = [R | A_j] agree in the first n - RC columns R (the family's n - rho
@@ -86,41 +119,41 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
 #pragma unroll
   for (int u = 0; u < NR; u++)
     R[u] = (lane < n && u < M) ? dev::ldS(S + (size_t)rlab * L + scol[u]) : make_double2(0.0, 0.0);
-  unsigned piv = 0;     // rows already used as pivots
-  int mystep = NC;      // the step at which this lane's row became the pivot (NC: never)
-  int parity = 0;
-  bool zero = false;
-  dev::cd det = make_double2(1.0, 0.0);
+  PivotState ps;
+  ps.piv = 0;
+  ps.mystep = NC;
+  ps.parity = 0;
+  ps.zero = false;
+  ps.det = make_double2(1.0, 0.0);
+  if (M > 0) select_pivot(ps, R[0], 0, n, lane);
+  // Step k: the multipliers of column k, then column k + 1 updated first and the pivot of
+  // step k + 1 chosen (with its reciprocal) before the other columns of step k, so that the
+  // chain of the next pivot (maximum, broadcast, reciprocal) overlaps independent updates.
+  // The values are those of the plain order: each entry sees the same operations.
 #pragma unroll
   for (int k = 0; k < NR; k++) {
     if (k >= M) break;
-    // pivot: the largest |re| + |im| in column k among the unused rows, by one warp-wide
-    // maximum of a key made of the measure's sign, exponent and leading 15 mantissa bits
-    // with (31 - lane) below them: a pivot within 2^-15 of the largest, the lowest row of
-    // those -- partial pivoting up to that tie tolerance; a zero measure keeps key bits 5..31
-    // zero, which is how an exactly zero pivot column shows
-    const bool cand = lane < n && !((piv >> lane) & 1);
-    const unsigned mkey = cand ? (((unsigned)__double2hiint(dev::abs1(R[k])) & ~31u) | (unsigned)(31 - lane)) : 0u;
-    const unsigned top = __reduce_max_sync(FULL, mkey);
-    const int p = 31 - (int)(top & 31u);
-    // the permutation's parity: p moves ahead of the unused rows that precede it
-    parity ^= __popc(~piv & ((1u << p) - 1u) & ((1u << n) - 1u)) & 1;
-    piv |= 1u << p;
-    mystep = lane == p ? k : mystep;
-    zero |= (top >> 5) == 0u;
-    const dev::cd pk = make_double2(__shfl_sync(FULL, R[k].x, p), __shfl_sync(FULL, R[k].y, p));
-    det = (k == 0) ? pk : dev::cmul(det, pk);
-    const dev::cd rc = dev::crcp(pk);
-    const bool act = lane < n && !((piv >> lane) & 1);
-    const dev::cd l = dev::cmul(R[k], rc);
+    const int p = ps.p;
+    const bool act = lane < n && !((ps.piv >> lane) & 1);
+    const dev::cd l = dev::cmul(R[k], ps.rc);
+    if (k + 1 < NR && k + 1 < M) {
+      const dev::cd pu = make_double2(__shfl_sync(FULL, R[k + 1].x, p), __shfl_sync(FULL, R[k + 1].y, p));
+      if (act) R[k + 1] = dev::cfms(l, pu, R[k + 1]);
+      select_pivot(ps, R[k + 1], k + 1, n, lane);
+    }
 #pragma unroll
-    for (int u = k + 1; u < NR; u++) {
+    for (int u = k + 2; u < NR; u++) {
       if (u >= M) break;
       const dev::cd pu = make_double2(__shfl_sync(FULL, R[u].x, p), __shfl_sync(FULL, R[u].y, p));
       if (act) R[u] = dev::cfms(l, pu, R[u]);
     }
     if (act) R[k] = l;  // this row's multiplier of step k
   }
+  const unsigned piv = ps.piv;
+  const int mystep = ps.mystep;
+  int parity = ps.parity;
+  bool zero = ps.zero;
+  dev::cd det = ps.det;
   // the RC rows left after the shared steps, ascending
   const unsigned rest = ~piv & ((1u << n) - 1u);
   int left[RC];
