@@ -154,8 +154,8 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   // one warp per block: the per-sink state (cached solves, member determinants, weight
   // accumulators) is all that lives in shared memory, so several warps fit per SM
   const int T = 32;
-  // cached solves [ysl][t] | member dets [F][kmax][t + 1]
-  auto smem_of = [&](int t) { return ((size_t)ysl * t + (size_t)kmax * F * (t + 1)) * sizeof(double2); };
+  // cached solves [ysl][t] (the member dets are global scratch of the block)
+  auto smem_of = [&](int t) { return (size_t)ysl * t * sizeof(double2); };
   if (smem_of(T) > 220 * 1024) {
     set_error("mhc_correlator_backward: a family is too large for the adjoint's shared memory; "
               "plan with a smaller opts.max_family");
@@ -187,6 +187,9 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
     return st;
   if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_accs), (size_t)ctas * kmax * T,
                       &d.bwd_accs_bytes)) != MHC_OK)
+    return st;
+  if ((st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_dets), (size_t)ctas * F * kmax * (T + 1),
+                      &d.bwd_dets_bytes)) != MHC_OK)
     return st;
   if (any_r2 && (st = dev_alloc(reinterpret_cast<double2**>(&d.bwd_r2),
                                 (size_t)ctas * kmax * max_rank * max_rank * T, &d.bwd_r2_bytes)) != MHC_OK)
@@ -241,6 +244,7 @@ extern "C" mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* con
   b.stage = reinterpret_cast<double2*>(d.bwd_stage);
   b.accs = reinterpret_cast<double2*>(d.bwd_accs);
   b.r2 = reinterpret_cast<double2*>(d.bwd_r2);
+  b.dets = reinterpret_cast<double2*>(d.bwd_dets);
   b.rk2 = max_rank * max_rank;
   const int nc = plan_ncmax(p);
   b.kinv = nullptr;

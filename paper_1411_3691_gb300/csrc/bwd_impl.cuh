@@ -37,6 +37,7 @@ struct BwdArgs {
   double2* stage;       // [cta][T][mn_max] shared-row cofactors of each sink, per block
   double2* accs;        // [cta][kmax][T] dw_src accumulators of each sink, per block
   double2* r2;          // [cta][kmax][rk2][T] member-row coefficients of rank-2/3 families
+  double2* dets;        // [cta][F][kmax][T + 1] member determinants, then gammas, of the block's sinks
   int rk2;              // coefficients per member: (largest rank)^2
   const double2* kinv;  // [W][Q][kistride]: B^{-1} row-major per flavour (two-sided blocks)
   int kistride;
@@ -994,9 +995,11 @@ __global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
   const int cta = blockIdx.x;
   const int W = cta / B.n_chunks, chunk = cta % B.n_chunks;
   const int mem0 = a.fam_info[4 * W], kW = a.fam_info[4 * W + 1];
-  // shared memory: y cache [ysl][T] | member dets [F][kmax][T + 1]
+  // shared memory: the y cache [ysl][T]; the member determinants [F][kmax][T + 1] live in
+  // global scratch of the block (L1-resident), which leaves the shared memory small enough
+  // for the registers to set the occupancy
   cd* Ysm = smem;
-  cd* Dets = Ysm + (size_t)B.ysl * T;
+  cd* Dets = B.dets + (size_t)cta * a.F * B.kmax * (T + 1);
   // dw_src accumulators: global scratch of this block (L1/L2-resident), which leaves the
   // shared memory to the data the scatter shares across lanes
   cd* AccS = B.accs + (size_t)cta * B.kmax * T;

@@ -55,6 +55,8 @@ struct DevicePlan {
   size_t bwd_accs_bytes = 0;
   double* bwd_r2 = nullptr;      // [cta][kmax][4][T] adjoint coefficients of two-row families
   size_t bwd_r2_bytes = 0;
+  double* bwd_dets = nullptr;    // [cta][F][kmax][T + 1] adjoint member determinants / gammas
+  size_t bwd_dets_bytes = 0;
   double* cw_tmp = nullptr;      // [4][2] real-weight correlators of mhc_correlator_cw
   double* kinv = nullptr;        // [W][Q][sum_f (n_f-1)^2] B^{-1} of two-sided blocks (adjoint)
   size_t kinv_bytes = 0;

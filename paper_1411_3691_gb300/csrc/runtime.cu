@@ -46,7 +46,7 @@ void free_device(DevicePlan& d) {
                   d.snk_lab, d.src_member, d.mem_family, d.w_src, d.w_snk, d.partials,
                   d.counters, d.bwd_rows, d.bwd_wsrc, d.bwd_wsnk, d.snk_order, d.snk_lab2,
                   d.snk_par2, d.snk_q, d.q_off, d.q_two, d.q_rank, d.kbuf, d.kguard, d.kinv, d.bwd_stage,
-                  d.bwd_accs, d.bwd_r2, d.cw_tmp};
+                  d.bwd_accs, d.bwd_r2, d.bwd_dets, d.cw_tmp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& bi : d.bwd_index) {
