@@ -986,8 +986,11 @@ __device__ __forceinline__ void dispatch_scatter(const FwdArgs& a, const BwdArgs
 #undef MHC_SC
 }
 
+// Blocks per SM: the n <= 8 class asks for 14 one-warp blocks (it compiles to 128 registers,
+// with spills): measured 7.88 ms per He-4-like call against 8.00 ms when asking for 16 and
+// 8.38 ms at the 12 blocks that 168 registers allowed.
 template <int NCMAX>
-__global__ void __launch_bounds__(32, 9) bwd_kernel(const BwdArgs B) {
+__global__ void __launch_bounds__(32, NCMAX <= 8 ? 14 : 9) bwd_kernel(const BwdArgs B) {
   const FwdArgs& a = B.a;
   extern __shared__ double2 smem[];
   const int T = blockDim.x;
