@@ -275,7 +275,7 @@ __device__ __forceinline__ void member_rows(const FwdArgs& a, int W, int m, int 
 // Per-flavour exponent scales of the member guard, packed 16 bits per flavour into two 64-bit
 // registers: an array indexed by the runtime flavour would live in local memory, and the
 // member loop reads it for every member and flavour.  (The n <= 8 class keeps the array:
-// measured faster there -- its member dots are short and its loads hit L1.)
+// its loads hit L1, and packing measured no faster there.)
 struct FlavourScalesArray {
   int e[MHC_FMAX];
   __device__ __forceinline__ void set(int f, int v) { e[f] = v; }
