@@ -53,10 +53,10 @@ NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # + 99.5 MB written per call of the copy (kfac_kernel, kfac_group_kernel, three fwd_kernel
 # launches, reduce_kernel).
 TRAFFIC = {
-    "large": {"bytes": 270.18e6 * 64,
+    "large": {"bytes": 269.78e6 * 64,
               "source": "ncu dram__bytes_read + dram__bytes_write of every kernel of one call of the "
                         "1/8-per-side copy (--workload large_small), x 64"},
-    "he4": {"bytes": 109.15e6,
+    "he4": {"bytes": 108.71e6,
             "source": "ncu dram__bytes_read + dram__bytes_write of every kernel of one call"},
 }
 

@@ -98,11 +98,11 @@ typedef struct {
                           until no merge lowers it; 1: first fit in term order
                           (each member joins the first family it fits).        0     */
   int32_t row_difference; /* 0: a member that fails the lemma guard is refactored from
-                          scratch; 1: a one-row member is first updated from the
-                          difference of its row and the nearest shared row
-                          (det [A; b] = det [A; b - a_r]: no cancellation when b
-                          nearly repeats a_r), guarded again, and refactored only
-                          if that guard fails too.                              0     */
+                          scratch; 1: a member of a one- or two-row family is first
+                          updated with one of its rows replaced by its difference
+                          from the nearest shared row (det [A; b] = det [A; b - a_r]:
+                          no cancellation when b nearly repeats a_r), guarded again,
+                          and refactored only if that guard fails too.          0     */
   int32_t reserved[3];
 } mhc_plan_opts;
 

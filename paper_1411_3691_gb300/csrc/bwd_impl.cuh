@@ -1077,11 +1077,13 @@ __global__ void __launch_bounds__(32, NCMAX <= 8 ? 14 : 9) bwd_kernel(const BwdA
           if (!fail)
             d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK,
                                             col, Ysm + (size_t)a.yoff[f] * T + tid, T, eys.get(f), a.kc, &fail);
-          if (fail && lemma && rho == 1 && n >= 2 && a.rowdiff) {  // as in the forward
+          if (fail && lemma && rho <= 2 && n >= rho + 1 && a.rowdiff) {  // as in the forward
             bool f2 = true;
-            const cd d2 = dev::rowdiff_det(a.S[f], a.L_f[f], n, a.mem_lab[((int64_t)m * a.F + f) * MHC_MAX_RANK],
-                                           a.fam_arow + (int64_t)W * a.Tn + a.off_f[f], col,
-                                           Ysm + (size_t)a.yoff[f] * T + tid, T, eys.get(f), a.kc, &f2);
+            const int32_t* mlab = a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK;
+            const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+            const cd* Yf = Ysm + (size_t)a.yoff[f] * T + tid;
+            const cd d2 = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Yf, T, eys.get(f), a.kc, &f2)
+                                   : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, col, Yf, T, eys.get(f), a.kc, &f2);
             if (!f2) {
               d = d2;
               fail = false;

@@ -419,6 +419,69 @@ static __device__ __noinline__ cd rowdiff_det(const cd* __restrict__ S, int L, i
 // |re| + |im| per shared row), the differences and the dot.
 __host__ __device__ constexpr int rowdiff_flops(int n) { return 3 * (n - 1) + 10 * n; }
 
+// The same for a two-row member (rows b_0, b_1) of a family of rank 2: with the shared rows'
+// null vectors z_1, z_2 (Y[q], Y[n + q]) and sd (Y[2n]), det [A; b_0; b_1] = sd det(B Z);
+// the member row nearer (relatively, in the sink's first column) to some shared row a_r is
+// replaced by its difference b_t - a_r, which leaves the determinant unchanged, and the
+// 2 x 2 determinant is formed as in member_det.  The lemma guard is taken again.
+static __device__ __noinline__ cd rowdiff2_det(const cd* __restrict__ S, int L, int n, const int32_t* __restrict__ mlab,
+                                        const int32_t* __restrict__ arow,
+                                        const int32_t* __restrict__ colp, const cd* __restrict__ Y,
+                                        int ys, int ey, int kc, bool* fail) {
+  const int c0 = colp[0];
+  int rt[2];
+  double dist[2], nrm[2];
+  for (int t = 0; t < 2; t++) {
+    const cd b0 = ldS(S + (size_t)mlab[t] * L + c0);
+    rt[t] = 0;
+    dist[t] = -1.0;
+    for (int i = 0; i < n - 2; i++) {
+      const cd x = ldS(S + (size_t)arow[i] * L + c0);
+      const double v = abs1(make_double2(b0.x - x.x, b0.y - x.y));
+      if (dist[t] < 0.0 || v < dist[t]) {
+        dist[t] = v;
+        rt[t] = i;
+      }
+    }
+    nrm[t] = abs1(b0);
+  }
+  const int t = (dist[1] * nrm[0] < dist[0] * nrm[1]) ? 1 : 0;  // the relatively nearer row
+  const cd* rd = S + (size_t)mlab[t] * L;      // the row that is replaced by a difference
+  const cd* ra = S + (size_t)arow[rt[t]] * L;
+  const cd* ro = S + (size_t)mlab[1 - t] * L;  // the other member row
+  cd dz1 = make_double2(0.0, 0.0), dz2 = dz1, oz1 = dz1, oz2 = dz1;
+  int ed = -4096, eo = -4096;
+  for (int q = 0; q < n; q++) {
+    const int c = colp[q];
+    const cd x = ldS(rd + c), z = ldS(ra + c), o = ldS(ro + c);
+    const cd del = make_double2(x.x - z.x, x.y - z.y);
+    const cd z1 = Y[q * ys], z2 = Y[(n + q) * ys];
+    ed = max(ed, expo(del));
+    eo = max(eo, expo(o));
+    dz1 = cfma(del, z1, dz1);
+    dz2 = cfma(del, z2, dz2);
+    oz1 = cfma(o, z1, oz1);
+    oz2 = cfma(o, z2, oz2);
+  }
+  // rows in the member's order: [difference; other] for t = 0, [other; difference] for t = 1
+  const cd d11 = t == 0 ? dz1 : oz1, d12 = t == 0 ? dz2 : oz2;
+  const cd d21 = t == 0 ? oz1 : dz1, d22 = t == 0 ? oz2 : dz2;
+  const cd dd = cfms(d12, d21, cmul(d11, d22));
+  const cd d = cmul(Y[2 * n * ys], dd);
+  *fail = expo(d) < ed + eo + ey - kc;
+  return d;
+}
+__host__ __device__ constexpr int rowdiff2_flops(int n) { return 6 * (n - 2) + 2 * n + 4 * (8 * n - 2) + 20; }
+
+// Scale exponent of a flavour's cached solve as its producers define it: rank 1 the largest
+// exponent of y's n entries; rank 2 the exponent of sd plus twice the largest exponent of
+// the null vectors' entries (at least 0, their unit entries).
+__device__ __forceinline__ int cached_scale(const cd* __restrict__ Y, int ys, int n, int rho) {
+  int e = rho == 1 ? -4096 : 0;
+  for (int q = 0; q < rho * n; q++) e = max(e, expo(Y[q * ys]));
+  return rho == 1 ? e : expo(Y[2 * n * ys]) + 2 * e;
+}
+
 // Two-sided update: the sink belongs to a sink family whose members share every column but
 // the last, so G = [[B, a], [g^T, alpha]] with B the block of shared rows and shared
 // columns.  By the Schur complement det G = alpha det B - g^T adj(B) a, i.e. det G = g' . y

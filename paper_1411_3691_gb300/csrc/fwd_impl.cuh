@@ -264,21 +264,24 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
   int32_t fail = have ? e.fail : 0;
   const int Q = a.snk_orig ? a.snk_q[j] : -1;
   if (a.rowdiff && have) {
-    // one-row members that failed the lemma guard (not the pivot guard): the row-difference
-    // update with the cached solve of the pair's sink (lane e.lane of this warp), whose scale
-    // exponent is the largest of its n entries
+    // members of one- and two-row families that failed the lemma guard (not the pivot
+    // guard): the row-difference update with the cached solve of the pair's sink (lane
+    // e.lane of this warp) and its scale exponent as the solve's producer defines it
     const unsigned cand = (unsigned)(e.fail & ~e.pguard);
     for (int f = 0; f < a.F; f++) {
       const int n = a.n_f[f];
-      if (!((cand >> f) & 1) || n < 2 || a.fam_rank[(int64_t)W * a.F + f] != 1) continue;
+      const int rho = a.fam_rank[(int64_t)W * a.F + f];
+      if (!((cand >> f) & 1) || rho > 2 || n < rho + 1) continue;
       const double2* Yf = Yw + (size_t)a.yoff[f] * T + e.lane;
-      int ey = -4096;
-      for (int q = 0; q < n; q++) ey = max(ey, dev::expo(Yf[q * T]));
+      const int ey = dev::cached_scale(Yf, T, n, rho);
       bool f2 = true;
       const int32_t* mlab = a.mem_lab + ((int64_t)e.member * a.F + f) * MHC_MAX_RANK;
-      const double2 d = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
-                                         cols + a.off_f[f], Yf, T, ey, a.kc, &f2);
-      rflops += dev::rowdiff_flops(n);
+      const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+      const double2 d = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, cols + a.off_f[f], Yf, T,
+                                                    ey, a.kc, &f2)
+                                 : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, cols + a.off_f[f], Yf, T,
+                                                     ey, a.kc, &f2);
+      rflops += rho == 1 ? dev::rowdiff_flops(n) : dev::rowdiff2_flops(n);
       if (!f2) {
         prod = dev::cmul(prod, d);
         fail &= ~(1 << f);
@@ -588,10 +591,11 @@ __global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pai
       if (!fail) {
         const int32_t* mlab = a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK;
         d = dev::dispatch_member<NCMAX>(n, rho, a.S[f], a.L_f[f], mlab, col, Y, T, ey, a.kc, &fail);
-        if (fail && rho == 1 && n >= 2 && a.rowdiff) {
+        if (fail && rho <= 2 && n >= rho + 1 && a.rowdiff) {
           bool f2 = true;
-          const double2 d2 = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], a.fam_arow + (int64_t)W * a.Tn + a.off_f[f],
-                                              col, Y, T, ey, a.kc, &f2);
+          const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
+          const double2 d2 = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Y, T, ey, a.kc, &f2)
+                                      : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, col, Y, T, ey, a.kc, &f2);
           if (!f2) {
             d = d2;
             fail = false;
