@@ -1082,8 +1082,12 @@ __global__ void __launch_bounds__(32, NCMAX <= 8 ? 14 : 9) bwd_kernel(const BwdA
             const int32_t* mlab = a.mem_lab + ((int64_t)m * a.F + f) * MHC_MAX_RANK;
             const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
             const cd* Yf = Ysm + (size_t)a.yoff[f] * T + tid;
-            const cd d2 = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Yf, T, eys.get(f), a.kc, &f2)
-                                   : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, col, Yf, T, eys.get(f), a.kc, &f2);
+            cd d2;
+            if constexpr (NCMAX >= 10)  // two-row families need n_f >= 10
+              d2 = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Yf, T, eys.get(f), a.kc, &f2)
+                            : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, col, Yf, T, eys.get(f), a.kc, &f2);
+            else
+              d2 = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Yf, T, eys.get(f), a.kc, &f2);
             if (!f2) {
               d = d2;
               fail = false;

@@ -277,10 +277,12 @@ __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& 
       bool f2 = true;
       const int32_t* mlab = a.mem_lab + ((int64_t)e.member * a.F + f) * MHC_MAX_RANK;
       const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
-      const double2 d = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, cols + a.off_f[f], Yf, T,
-                                                    ey, a.kc, &f2)
-                                 : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, cols + a.off_f[f], Yf, T,
-                                                     ey, a.kc, &f2);
+      double2 d;
+      if constexpr (NCMAX >= 10)  // two-row families need n_f >= 10
+        d = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, cols + a.off_f[f], Yf, T, ey, a.kc, &f2)
+                     : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, cols + a.off_f[f], Yf, T, ey, a.kc, &f2);
+      else
+        d = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, cols + a.off_f[f], Yf, T, ey, a.kc, &f2);
       rflops += rho == 1 ? dev::rowdiff_flops(n) : dev::rowdiff2_flops(n);
       if (!f2) {
         prod = dev::cmul(prod, d);
@@ -594,8 +596,12 @@ __global__ void __launch_bounds__(64) pair_kernel(const FwdArgs a, int64_t n_pai
         if (fail && rho <= 2 && n >= rho + 1 && a.rowdiff) {
           bool f2 = true;
           const int32_t* arow = a.fam_arow + (int64_t)W * a.Tn + a.off_f[f];
-          const double2 d2 = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Y, T, ey, a.kc, &f2)
-                                      : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, col, Y, T, ey, a.kc, &f2);
+          double2 d2;
+          if constexpr (NCMAX >= 10)  // two-row families need n_f >= 10
+            d2 = rho == 1 ? dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Y, T, ey, a.kc, &f2)
+                          : dev::rowdiff2_det(a.S[f], a.L_f[f], n, mlab, arow, col, Y, T, ey, a.kc, &f2);
+          else
+            d2 = dev::rowdiff_det(a.S[f], a.L_f[f], n, mlab[0], arow, col, Y, T, ey, a.kc, &f2);
           if (!f2) {
             d = d2;
             fail = false;
