@@ -5,10 +5,12 @@
 // sink.  Per flavour a thread factorises the family's shared rows against its sink's
 // columns (shared_rows) and caches y = det(G) G^{-1} e_r in shared memory; then every
 // member of the family costs one O(n) dot product per flavour (member_det), Sec. 2.1.
-// Members whose lemma factor or whose family pivots fail the guards go to a per-warp
-// queue and are refactored from scratch 32 at a time, one per lane, so the FP64 pipe
-// stays fully occupied.  Thread sums are reduced in a fixed order into one partial per
-// work item (and by reduce_kernel into C): bitwise reproducible.
+// Two-sided blocks (a family against a sink family) take y from factors stored once per
+// block (kapply*).  Members whose lemma factor or whose family pivots fail the guards go
+// to a per-warp queue and are refactored from scratch 32 at a time -- pairs that share the
+// member and the sink family's columns as one group (group_fresh), so the FP64 pipe stays
+// occupied.  Thread sums are reduced in a fixed order into one partial per work item (and
+// by reduce_kernel into C): bitwise reproducible.
 #pragma once
 
 #include "kernels.cuh"
@@ -249,9 +251,11 @@ __device__ __forceinline__ dev::cd group_fresh(const FwdArgs& a, int W, int f, i
 
 // Refactor one pair per lane (the lanes with have; e: the pair, j: its sink position):
 // the product of the flavours that passed, times fresh determinants of the flavours that
-// failed, accumulated into acc.  Pairs that share a member and a two-sided sink family
-// (one changed column, rank-1 family) are factorised together (group_fresh); the others
-// one per lane.  Called by the whole warp.
+// failed, accumulated into acc.  With a.rowdiff the row-difference update is tried first
+// for members of one- and two-row families.  Pairs that share a member and a two-sided sink
+// family with one or two changed columns (n <= 18) are factorised together (group_fresh);
+// the others one per lane.  Yw: the warp's cached solves (lane l at Yw + l, stride
+// blockDim.x); wk: the warp's scratch for group_fresh.  Called by the whole warp.
 template <int NCMAX>
 __device__ void process_pairs(const FwdArgs& a, int W, bool have, const QEntry& e, int64_t j,
                               const double2* Yw, double2* wk, double2& acc, unsigned long long& rflops,
