@@ -257,11 +257,16 @@ mhc_status mhc_correlator_cw(mhc_plan_t plan, const double* const* S_f, const do
  * which is PyTorch's convention for the gradient of a real loss.  g_out_dev is a device
  * pointer to 2 doubles.  Any of dS_f (the whole array or single entries), dw_src_dev or
  * dw_snk_dev may be NULL to skip that output.  The dS_f buffers must not alias each
- * other.  Families of two or three changed rows are differentiated through the null
- * vectors of their shared rows; where those rows fail the pivot guard for a sink, the null
- * vectors are recomputed with complete pivoting, and where the shared rows are exactly
+ * other.  Families of k = 2 ... MHC_MAX_RANK changed rows are differentiated through the
+ * null vectors of their shared rows; where those rows fail the pivot guard for a sink, the
+ * null vectors are recomputed with complete pivoting, and where the shared rows are exactly
  * rank-deficient (every member's determinant and member-row cofactor is then 0) the shared
- * rows' cofactors come from signed minors.  Not in the paper.
+ * rows' cofactors come from signed minors.  A member whose lemma guard fails takes its
+ * determinant (which weights the other flavours' cofactors) from a fresh LU, or with
+ * opts.row_difference from the row-difference update first, as in the forward.  The plan
+ * holds the adjoint's workspace (per block of sinks: row accumulators, staged cofactors,
+ * member determinants; allocated on the first call and grown when needed): calls with the
+ * same plan must not overlap on the GPU.  Not in the paper.
  */
 mhc_status mhc_correlator_backward(mhc_plan_t plan, const double* const* S_f,
                                    const double* w_src_dev, const double* w_snk_dev,
